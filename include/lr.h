@@ -1,0 +1,206 @@
+/*
+ * lr.h -- C ABI of a GB300 (sm_103a) implementation of the exact order-independent-
+ * transparency quad rasteriser of "LucidRaster: GPU Software Rasterizer for Exact
+ * Order-Independent Transparency" (arXiv 2405.13364).
+ *
+ * The pipeline is the paper's sort-middle design (Sec. 2, "Pipeline description"):
+ * quad setup (Stage 1), 32x32-pixel binning (Stage 2), per-bin rasterisation with a
+ * two-stage sort and blending (Stage 3), plus an exact fallback for pixels whose order
+ * the fixed-size sorter cannot guarantee (Sec. 2, "Sample blending": misordered pixels
+ * "could be registered and afterwards processed by a slower, conservative algorithm").
+ *
+ * Conventions for every entry point:
+ *  - Plain pointers only. Pointers documented as "device" must point to memory of the
+ *    context's CUDA device; "host" pointers to ordinary host memory.
+ *  - The caller owns every input, output and workspace buffer; the library owns only the
+ *    lr_ctx object and what it allocates internally (a small control buffer, serving
+ *    state). Rendering calls are asynchronous on the given stream: they return once the
+ *    work is enqueued, and the caller must keep all buffers alive and untouched until the
+ *    stream has finished it.
+ *  - Every function returns an lr_status and never aborts the process. Errors found
+ *    while the GPU runs (capacity exceeded, out-of-range vertex indices) are recorded in
+ *    the workspace and reported by lr_get_stats(), which synchronises.
+ *  - Not thread-safe per context, except lr_submit / lr_poll which may be called from
+ *    any thread.
+ */
+#ifndef LR_H_
+#define LR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lr_ctx lr_ctx;            /* opaque, owned by the library */
+typedef struct CUstream_st* lr_stream;   /* a cudaStream_t; NULL = the legacy default stream */
+
+typedef enum {
+  LR_OK = 0,
+  LR_PENDING = 1,            /* lr_poll: the request has not finished yet */
+  LR_ERR_INVALID_ARG = -1,   /* bad argument, or out-of-range vertex index found on the GPU */
+  LR_ERR_TOO_LARGE = -2,     /* width/height above the context's maximum, or too many quads */
+  LR_ERR_OOM = -3,           /* a device allocation failed / workspace too small */
+  LR_ERR_CUDA = -4,          /* a CUDA runtime call failed (see lr_last_error) */
+  LR_ERR_TIMEOUT = -5,       /* lr_poll's time limit ran out */
+  LR_ERR_OVERFLOW = -6,      /* the workspace's bin-reference capacity was exceeded */
+  LR_ERR_UNSUPPORTED = -7    /* option combination not implemented */
+} lr_status;
+
+enum { LR_COLOR_FLAT = 0, LR_COLOR_VERTEX = 1 };
+
+/* lr_config.flags */
+enum {
+  LR_FLAG_TIMING = 1        /* record per-stage CUDA events; lr_get_stats reports stage_ms */
+};
+
+/* Creation-time parameters. Zero selects the default. */
+typedef struct {
+  int32_t max_width;         /* default 2560 (the paper's limit is 2560x2048, Sec. 4) */
+  int32_t max_height;        /* default 2048 */
+  int32_t sorter_k;          /* per-pixel fixed-size sorter capacity K (the paper's "depth
+                                filter", Sec. 2 "Sample blending", size 3): one of
+                                1, 2, 3, 4, 6, 8, 12; default 3 */
+  int32_t raster_ctas_per_sm;/* persistent rasteriser CTAs per SM; default: occupancy limit */
+  int32_t ref_factor;        /* bin-reference capacity per quad in the workspace; default 4 */
+  int32_t flags;             /* LR_FLAG_* */
+  int32_t device;            /* CUDA device ordinal; -1 or 0 = current device */
+} lr_config;
+
+/* A quad scene (Sec. 2: quads, not triangles, are the input primitive). Device memory. */
+typedef struct {
+  const float* positions;    /* device f32[V][3], world space */
+  int64_t num_vertices;      /* V */
+  const uint32_t* indices;   /* device u32[Q][4] vertex indices, or NULL: quad q uses
+                                vertices 4q..4q+3 (then V >= 4Q) */
+  int64_t num_quads;         /* Q */
+  const float* colors;       /* device, straight RGBA: f32[Q][4] (LR_COLOR_FLAT) or
+                                f32[V][4] (LR_COLOR_VERTEX, interpolated perspective-correctly) */
+  int32_t color_mode;
+  int32_t reserved;
+} lr_quads;
+
+/* Camera: clip = view_proj * (x, y, z, 1), row-major; clip.w is the view depth (> 0 in
+ * front). Quads with any vertex outside near_z <= w <= far_z are culled whole. */
+typedef struct {
+  float view_proj[16];
+  float near_z, far_z;
+} lr_camera;
+
+/* Outputs of one view. rgba is required; the rest are optional (NULL). Device memory,
+ * row 0 = top of the image. */
+typedef struct {
+  float* rgba;               /* f32[H][W][4]: composited straight RGB and coverage alpha */
+  uint8_t* rgba8;            /* u8[H][W][4]: rint(clamp(v, 0, 1) * 255) */
+  uint32_t* frag_count;      /* u32[H][W]: number of fragments covering the pixel */
+  uint64_t* cov_hash;        /* u64[H][W]: sum of splitmix64(2 * quad + triangle) */
+} lr_target;
+
+/* One view of a batch: a scene, a camera, a resolution and its outputs. */
+typedef struct {
+  lr_quads quads;
+  lr_camera camera;
+  int32_t width, height;
+  lr_target target;
+} lr_view;
+
+typedef struct {
+  int32_t status;            /* sticky device-side status of the last render (lr_status) */
+  int32_t n_views;
+  int64_t quads_in;
+  int64_t quads_visible;
+  int64_t culled[8];         /* by reason: 1 bad index, 2 non-finite, 3 depth, 4 guard band,
+                                5 degenerate, 6 no pixel centre */
+  int64_t bin_refs;          /* (quad, bin) references produced by binning */
+  int64_t bin_refs_capacity; /* what the workspace could hold */
+  int64_t bins_nonempty;
+  int64_t bins_high;         /* bins sorted by the high-density (global-memory) path */
+  int64_t max_bin_refs;
+  int64_t fragments;         /* covering (pixel, quad, triangle) fragments */
+  int64_t overflow_pixels;   /* pixels re-done by the exact full sort */
+  float stage_ms[8];         /* with LR_FLAG_TIMING: setup, count, scan, scatter, sort,
+                                raster, overflow, total */
+} lr_stats;
+
+/* Byte offsets, inside a workspace, of the per-quad records written by the setup stage and
+ * of the binning arrays (for tests and inspection; valid after the render's stream has
+ * finished and until the workspace is reused):
+ *   rec_xy    i32[Q][8]  snapped vertex positions X0 Y0 X1 Y1 X2 Y2 X3 Y3 (1/256 pixel)
+ *   rec_q     f32[Q][4]  1/w of each vertex
+ *   rec_rect  u32[Q][2]  pixel-centre AABB: px0 | px1 << 16, py0 | py1 << 16
+ *                        (0x0000FFFF, 0x0000FFFF for a culled quad)
+ *   rec_info  u32[Q]     bit 0/1: triangle 0/1 has non-zero area, bit 2: spans more than
+ *                        2x2 bins, bits 8..11: cull reason (0 = visible)
+ *   bin_off   u32[bins+1] start of each bin's reference list in refs
+ *   refs      u64[capacity] per-bin reference lists, sorted front to back
+ * Quads, bins and pixels of a batch are numbered view after view. */
+typedef struct {
+  size_t rec_xy, rec_q, rec_rect, rec_info, bin_count, bin_off, refs;
+  int64_t total_quads, total_bins, refs_capacity;
+} lr_ws_layout;
+
+/* Create / destroy a context bound to one CUDA device. */
+lr_status lr_create(const lr_config* config, lr_ctx** out_ctx);
+lr_status lr_destroy(lr_ctx* ctx);
+
+/* Bytes of workspace lr_render needs for a scene of num_quads quads at width x height
+ * (host call, no GPU work). The workspace holds fixed-size arrays plus the (quad, bin)
+ * reference lists of binning, whose capacity is whatever the workspace holds beyond the
+ * fixed part; this function sizes it at ref_factor references per quad. A scene whose
+ * quads overlap more bins reports LR_ERR_OVERFLOW from lr_get_stats, with stats.bin_refs
+ * = the number of references it needed; lr_workspace_size_refs gives the bytes for that. */
+lr_status lr_workspace_size(const lr_ctx* ctx, int64_t num_quads, int32_t width, int32_t height,
+                            size_t* out_bytes);
+
+/* Same for a batch of views (host memory array of n_views lr_view). */
+lr_status lr_workspace_size_batch(const lr_ctx* ctx, int32_t n_views, const lr_view* views,
+                                  size_t* out_bytes);
+
+/* Bytes of workspace for a batch whose binning produces bin_refs references (-1: the
+ * default capacity of ref_factor per quad). */
+lr_status lr_workspace_size_refs(const lr_ctx* ctx, int32_t n_views, const lr_view* views,
+                                 int64_t bin_refs, size_t* out_bytes);
+
+/* Render one frame (Sec. 2, all three stages): out_rgba = device f32[H][W][4].
+ * workspace: device, >= lr_workspace_size bytes, 256-byte aligned, owned by the caller.
+ * Enqueued on stream; returns LR_ERR_INVALID_ARG / LR_ERR_TOO_LARGE / LR_ERR_OOM for bad
+ * arguments before any GPU work. */
+lr_status lr_render(lr_ctx* ctx, const lr_quads* quads, const lr_camera* camera, int32_t width,
+                    int32_t height, float* out_rgba, void* workspace, size_t workspace_bytes,
+                    lr_stream stream);
+
+/* Render n_views views (host array) with one launch per pipeline stage: every stage's
+ * kernel processes all views' quads, bins and pixels together (persistent multi-view
+ * launch). The launch sequence contains no host synchronisation, so it can be captured
+ * in a CUDA graph. */
+lr_status lr_render_batch(lr_ctx* ctx, int32_t n_views, const lr_view* views, void* workspace,
+                          size_t workspace_bytes, lr_stream stream);
+
+/* Backward pass of the compositing with respect to flat per-quad RGBA.
+ * grad_out: device f32[H][W][4] = dL/d(R, G, B, A) of the rendered image.
+ * fwd_rgba: device f32[H][W][4] = the forward image of the same scene (as lr_render wrote
+ *           it); the per-pixel fragment order is recomputed, not stored.
+ * grad_colors: device f32[Q][4]; gradients are ADDED to it (zero it first).
+ * Only LR_COLOR_FLAT scenes (LR_ERR_UNSUPPORTED otherwise). */
+lr_status lr_render_backward(lr_ctx* ctx, const lr_quads* quads, const lr_camera* camera,
+                             int32_t width, int32_t height, const float* fwd_rgba,
+                             const float* grad_out, float* grad_colors, void* workspace,
+                             size_t workspace_bytes, lr_stream stream);
+
+/* Layout of a workspace of workspace_bytes bytes for this batch (host call). */
+lr_status lr_workspace_layout(const lr_ctx* ctx, int32_t n_views, const lr_view* views,
+                              size_t workspace_bytes, lr_ws_layout* out);
+
+/* Wait for the last render / backward issued on this context and report its counters
+ * (synchronises that stream). stats may be NULL to only fetch the status. */
+lr_status lr_get_stats(lr_ctx* ctx, lr_stats* stats);
+
+/* Human-readable description of the last error on this context (never NULL). */
+const char* lr_last_error(const lr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LR_H_ */

@@ -1,0 +1,244 @@
+"""GB300-native exact order-independent-transparency quad rasteriser (LucidRaster,
+arXiv 2405.13364): Python layer over the C ABI in include/lr.h.
+
+PyTorch is used for device memory and streams only; every pipeline stage runs in the
+CUDA library (liblr.so). Nothing here computes pixels.
+
+    r = Renderer(sorter_k=3)
+    scene = DeviceScene.from_arrays(positions, indices, colors, color_mode, view_proj, near, far)
+    out = r.render(scene, 1920, 1080)          # {'rgba': f32[H][W][4] on the GPU, ...}
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import torch
+
+from . import _binding as B
+from ._binding import (LR_COLOR_FLAT, LR_COLOR_VERTEX, LR_ERR_OVERFLOW, LR_FLAG_TIMING, LR_OK,
+                       LrError, lr_camera, lr_config, lr_quads, lr_stats, lr_target, lr_view)
+
+__all__ = ["Renderer", "DeviceScene", "LrError", "LR_COLOR_FLAT", "LR_COLOR_VERTEX", "load_library"]
+
+
+def load_library():
+    """Load (and if needed build) liblr.so; raises if the CUDA library is unavailable."""
+    return B.load()
+
+
+def _ptr(t):
+    return 0 if t is None else int(t.data_ptr())
+
+
+@dataclasses.dataclass
+class DeviceScene:
+    """A quad scene resident on the GPU (tensors are kept alive by this object)."""
+
+    positions: torch.Tensor            # f32[V][3]
+    indices: torch.Tensor | None       # i32/u32[Q][4] or None
+    colors: torch.Tensor               # f32[Q][4] or f32[V][4]
+    color_mode: int
+    view_proj: tuple                   # 16 floats, row-major
+    near: float
+    far: float
+
+    @property
+    def num_quads(self) -> int:
+        return int(self.indices.shape[0]) if self.indices is not None else int(self.positions.shape[0] // 4)
+
+    @classmethod
+    def from_arrays(cls, positions, indices, colors, color_mode, view_proj, near, far,
+                    device="cuda"):
+        def dev(a, dtype):
+            t = torch.as_tensor(a)
+            if t.dtype != dtype:
+                t = t.to(dtype)
+            return t.to(device).contiguous()
+
+        pos = dev(positions, torch.float32).reshape(-1, 3)
+        idx = None
+        if indices is not None:
+            idx_t = torch.as_tensor(indices)
+            if idx_t.dtype != torch.int32:
+                idx_t = idx_t.to(torch.int64).to(torch.int32)
+            idx = idx_t.to(device).contiguous().reshape(-1, 4)
+        col = dev(colors, torch.float32).reshape(-1, 4)
+        vp = tuple(float(x) for x in torch.as_tensor(view_proj, dtype=torch.float32).reshape(-1).tolist())
+        return cls(pos, idx, col, int(color_mode), vp, float(near), float(far))
+
+    @classmethod
+    def from_scene(cls, scene, device="cuda"):
+        """From any object with positions / indices / colors / color_mode / view_proj /
+        near / far attributes (e.g. the seeded generators' Scene)."""
+        return cls.from_arrays(scene.positions, scene.indices, scene.colors, scene.color_mode,
+                               scene.view_proj, scene.near, scene.far, device=device)
+
+    def with_colors(self, colors: torch.Tensor) -> "DeviceScene":
+        return dataclasses.replace(self, colors=colors.contiguous())
+
+    def quads_struct(self) -> lr_quads:
+        return lr_quads(_ptr(self.positions), int(self.positions.shape[0]), _ptr(self.indices),
+                        self.num_quads, _ptr(self.colors), self.color_mode, 0)
+
+    def camera_struct(self) -> lr_camera:
+        cam = lr_camera()
+        for i, v in enumerate(self.view_proj):
+            cam.view_proj[i] = v
+        cam.near_z = self.near
+        cam.far_z = self.far
+        return cam
+
+
+class Outputs(dict):
+    """Per-view outputs: 'rgba' and optionally 'rgba8', 'count', 'hash' (device tensors)."""
+
+
+class Renderer:
+    """Owns an lr_ctx and a growable workspace on one CUDA device."""
+
+    def __init__(self, sorter_k: int = 3, max_width: int = 2560, max_height: int = 2048,
+                 timing: bool = False, ref_factor: int = 4, raster_ctas_per_sm: int = 0,
+                 device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        B.load()
+        with torch.cuda.device(self.device):
+            cfg = lr_config(max_width, max_height, sorter_k, raster_ctas_per_sm, ref_factor,
+                            LR_FLAG_TIMING if timing else 0, self.device.index)
+            self.ctx = B.lr_create(cfg)
+        self.sorter_k = sorter_k
+        self._ws = None
+        self._ws_bytes = 0
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            B.lr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- workspace -----------------------------------------------------------------------
+    def workspace(self, nbytes: int):
+        """A 256-byte aligned device buffer of at least nbytes (grown, never shrunk)."""
+        if self._ws is None or self._ws_bytes < nbytes:
+            self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            self._ws_bytes = nbytes
+        base = int(self._ws.data_ptr())
+        return (base + 255) & ~255, self._ws_bytes
+
+    # ---- views -----------------------------------------------------------------------------
+    def make_outputs(self, width, height, rgba8=False, count=False, hash=False) -> Outputs:
+        o = Outputs()
+        o["rgba"] = torch.empty((height, width, 4), dtype=torch.float32, device=self.device)
+        if rgba8:
+            o["rgba8"] = torch.empty((height, width, 4), dtype=torch.uint8, device=self.device)
+        if count:
+            o["count"] = torch.empty((height, width), dtype=torch.int32, device=self.device)
+        if hash:
+            o["hash"] = torch.empty((height, width), dtype=torch.int64, device=self.device)
+        return o
+
+    @staticmethod
+    def view_struct(scene: DeviceScene, width: int, height: int, out: Outputs) -> lr_view:
+        tgt = lr_target(_ptr(out["rgba"]), _ptr(out.get("rgba8")), _ptr(out.get("count")),
+                        _ptr(out.get("hash")))
+        return lr_view(scene.quads_struct(), scene.camera_struct(), width, height, tgt)
+
+    def render_views(self, views, stream=None, check: bool = True):
+        """Render lr_view structs with one lr_render_batch call; grows the workspace and
+        retries once if binning needed more references than the workspace held."""
+        stream = torch.cuda.current_stream(self.device) if stream is None else stream
+        need = B.lr_workspace_size_batch(self.ctx, views)
+        for _ in range(3):
+            ptr, nbytes = self.workspace(need)
+            B.lr_render_batch(self.ctx, views, ptr, nbytes, stream.cuda_stream)
+            if not check:
+                return None
+            st = B.lr_get_stats(self.ctx, raise_on_error=False)
+            if st.status == LR_ERR_OVERFLOW:
+                need = B.lr_workspace_size_refs(self.ctx, views, int(st.bin_refs * 1.25) + 1024)
+                continue
+            if st.status != LR_OK:
+                raise LrError(st.status, B.lr_last_error(self.ctx))
+            return st
+        raise LrError(LR_ERR_OVERFLOW, "bin references kept exceeding the workspace")
+
+    def render(self, scene: DeviceScene, width: int, height: int, rgba8=False, count=False,
+               hash=False, stream=None, check: bool = True) -> Outputs:
+        out = self.make_outputs(width, height, rgba8, count, hash)
+        self.render_views([self.view_struct(scene, width, height, out)], stream, check)
+        return out
+
+    def render_batch(self, items, stream=None, check: bool = True, **outputs):
+        """items: list of (DeviceScene, width, height). One launch per stage for all."""
+        outs = [self.make_outputs(w, h, **outputs) for _, w, h in items]
+        views = [self.view_struct(s, w, h, o) for (s, w, h), o in zip(items, outs)]
+        self.render_views(views, stream, check)
+        return outs
+
+    def stats(self) -> dict:
+        st = B.lr_get_stats(self.ctx, raise_on_error=False)
+        names = ["setup", "count", "scan", "scatter", "sort", "raster", "overflow", "total"]
+        return dict(status=st.status, n_views=st.n_views, quads_in=st.quads_in,
+                    quads_visible=st.quads_visible, culled=list(st.culled), bin_refs=st.bin_refs,
+                    bin_refs_capacity=st.bin_refs_capacity, bins_nonempty=st.bins_nonempty,
+                    bins_high=st.bins_high, max_bin_refs=st.max_bin_refs, fragments=st.fragments,
+                    overflow_pixels=st.overflow_pixels,
+                    stage_ms={n: st.stage_ms[i] for i, n in enumerate(names)})
+
+    # ---- differentiation ----------------------------------------------------------------------
+    def render_backward(self, scene: DeviceScene, width: int, height: int, fwd_rgba: torch.Tensor,
+                        grad_out: torch.Tensor, stream=None, check: bool = True) -> torch.Tensor:
+        """dL/d(flat per-quad RGBA) given dL/d(image); the fragment order is recomputed."""
+        stream = torch.cuda.current_stream(self.device) if stream is None else stream
+        grad = torch.zeros((scene.num_quads, 4), dtype=torch.float32, device=self.device)
+        fwd_rgba = fwd_rgba.contiguous()
+        grad_out = grad_out.to(torch.float32).contiguous()
+        out = Outputs(rgba=fwd_rgba)
+        view = self.view_struct(scene, width, height, out)
+        need = B.lr_workspace_size_batch(self.ctx, [view])
+        for _ in range(3):
+            ptr, nbytes = self.workspace(need)
+            B.lr_render_backward(self.ctx, scene.quads_struct(), scene.camera_struct(), width, height,
+                                 _ptr(fwd_rgba), _ptr(grad_out), _ptr(grad), ptr, nbytes,
+                                 stream.cuda_stream)
+            if not check:
+                return grad
+            st = B.lr_get_stats(self.ctx, raise_on_error=False)
+            if st.status == LR_ERR_OVERFLOW:
+                need = B.lr_workspace_size_refs(self.ctx, [view], int(st.bin_refs * 1.25) + 1024)
+                grad.zero_()
+                continue
+            if st.status != LR_OK:
+                raise LrError(st.status, B.lr_last_error(self.ctx))
+            return grad
+        raise LrError(LR_ERR_OVERFLOW, "bin references kept exceeding the workspace")
+
+
+class _Composite(torch.autograd.Function):
+    @staticmethod
+    def forward(actx, colors, renderer, scene, width, height):
+        s = scene.with_colors(colors.detach().to(torch.float32).contiguous())
+        out = renderer.render(s, width, height)["rgba"]
+        actx.renderer, actx.scene, actx.size = renderer, s, (width, height)
+        actx.save_for_backward(out)
+        return out
+
+    @staticmethod
+    def backward(actx, grad_out):
+        (out,) = actx.saved_tensors
+        w, h = actx.size
+        g = actx.renderer.render_backward(actx.scene, w, h, out, grad_out)
+        return g, None, None, None, None
+
+
+def composite(colors: torch.Tensor, renderer: Renderer, scene: DeviceScene, width: int,
+              height: int) -> torch.Tensor:
+    """Differentiable render w.r.t. flat per-quad RGBA colors f32[Q][4] (CUDA tensor).
+    Coverage and depth order are exact and piecewise constant: they get no gradient."""
+    return _Composite.apply(colors, renderer, scene, width, height)

@@ -1,0 +1,216 @@
+"""ctypes binding of the C ABI declared in include/lr.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and forwards plain
+pointers and sizes. The library must be built (``paper_2405_13364_gb300._build``); there
+is no fallback: loading fails loudly if liblr.so is missing or cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+LR_OK = 0
+LR_PENDING = 1
+LR_ERR_INVALID_ARG = -1
+LR_ERR_TOO_LARGE = -2
+LR_ERR_OOM = -3
+LR_ERR_CUDA = -4
+LR_ERR_TIMEOUT = -5
+LR_ERR_OVERFLOW = -6
+LR_ERR_UNSUPPORTED = -7
+
+STATUS_NAMES = {0: "LR_OK", 1: "LR_PENDING", -1: "LR_ERR_INVALID_ARG", -2: "LR_ERR_TOO_LARGE",
+                -3: "LR_ERR_OOM", -4: "LR_ERR_CUDA", -5: "LR_ERR_TIMEOUT", -6: "LR_ERR_OVERFLOW",
+                -7: "LR_ERR_UNSUPPORTED"}
+
+LR_COLOR_FLAT = 0
+LR_COLOR_VERTEX = 1
+LR_FLAG_TIMING = 1
+
+
+class LrError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class lr_config(ctypes.Structure):
+    _fields_ = [("max_width", ctypes.c_int32), ("max_height", ctypes.c_int32),
+                ("sorter_k", ctypes.c_int32), ("raster_ctas_per_sm", ctypes.c_int32),
+                ("ref_factor", ctypes.c_int32), ("flags", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class lr_quads(ctypes.Structure):
+    _fields_ = [("positions", ctypes.c_void_p), ("num_vertices", ctypes.c_int64),
+                ("indices", ctypes.c_void_p), ("num_quads", ctypes.c_int64),
+                ("colors", ctypes.c_void_p), ("color_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class lr_camera(ctypes.Structure):
+    _fields_ = [("view_proj", ctypes.c_float * 16), ("near_z", ctypes.c_float),
+                ("far_z", ctypes.c_float)]
+
+
+class lr_target(ctypes.Structure):
+    _fields_ = [("rgba", ctypes.c_void_p), ("rgba8", ctypes.c_void_p),
+                ("frag_count", ctypes.c_void_p), ("cov_hash", ctypes.c_void_p)]
+
+
+class lr_view(ctypes.Structure):
+    _fields_ = [("quads", lr_quads), ("camera", lr_camera), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("target", lr_target)]
+
+
+class lr_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n_views", ctypes.c_int32),
+                ("quads_in", ctypes.c_int64), ("quads_visible", ctypes.c_int64),
+                ("culled", ctypes.c_int64 * 8), ("bin_refs", ctypes.c_int64),
+                ("bin_refs_capacity", ctypes.c_int64), ("bins_nonempty", ctypes.c_int64),
+                ("bins_high", ctypes.c_int64), ("max_bin_refs", ctypes.c_int64),
+                ("fragments", ctypes.c_int64), ("overflow_pixels", ctypes.c_int64),
+                ("stage_ms", ctypes.c_float * 8)]
+
+
+class lr_ws_layout(ctypes.Structure):
+    _fields_ = [("rec_xy", ctypes.c_size_t), ("rec_q", ctypes.c_size_t), ("rec_rect", ctypes.c_size_t),
+                ("rec_info", ctypes.c_size_t), ("bin_count", ctypes.c_size_t),
+                ("bin_off", ctypes.c_size_t), ("refs", ctypes.c_size_t),
+                ("total_quads", ctypes.c_int64), ("total_bins", ctypes.c_int64),
+                ("refs_capacity", ctypes.c_int64)]
+
+
+# every entry point declared in include/lr.h, with its ctypes signature
+_P = ctypes.c_void_p
+_SIGNATURES = {
+    "lr_create": (ctypes.c_int, [ctypes.POINTER(lr_config), ctypes.POINTER(_P)]),
+    "lr_destroy": (ctypes.c_int, [_P]),
+    "lr_workspace_size": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_size_t)]),
+    "lr_workspace_size_batch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(lr_view),
+                                               ctypes.POINTER(ctypes.c_size_t)]),
+    "lr_workspace_size_refs": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(lr_view),
+                                              ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
+    "lr_render": (ctypes.c_int, [_P, ctypes.POINTER(lr_quads), ctypes.POINTER(lr_camera),
+                                 ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_size_t, _P]),
+    "lr_render_batch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(lr_view), _P,
+                                       ctypes.c_size_t, _P]),
+    "lr_render_backward": (ctypes.c_int, [_P, ctypes.POINTER(lr_quads), ctypes.POINTER(lr_camera),
+                                          ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P,
+                                          ctypes.c_size_t, _P]),
+    "lr_workspace_layout": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(lr_view),
+                                           ctypes.c_size_t, ctypes.POINTER(lr_ws_layout)]),
+    "lr_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(lr_stats)]),
+    "lr_last_error": (ctypes.c_char_p, [_P]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblr.so (building it first when missing and nvcc is available)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} is missing")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(ctx, status: int, what: str):
+    if status != LR_OK:
+        msg = load().lr_last_error(ctx) if ctx else b""
+        raise LrError(status, f"{what}: {(msg or b'').decode(errors='replace')}")
+
+
+def lr_create(config: lr_config | None = None):
+    lib = load()
+    out = _P()
+    st = lib.lr_create(ctypes.byref(config) if config is not None else None, ctypes.byref(out))
+    _check(None, st, "lr_create")
+    return out
+
+
+def lr_destroy(ctx):
+    _check(None, load().lr_destroy(ctx), "lr_destroy")
+
+
+def lr_workspace_size(ctx, num_quads: int, width: int, height: int) -> int:
+    n = ctypes.c_size_t()
+    _check(ctx, load().lr_workspace_size(ctx, num_quads, width, height, ctypes.byref(n)),
+           "lr_workspace_size")
+    return n.value
+
+
+def lr_workspace_size_batch(ctx, views) -> int:
+    arr = (lr_view * len(views))(*views)
+    n = ctypes.c_size_t()
+    _check(ctx, load().lr_workspace_size_batch(ctx, len(views), arr, ctypes.byref(n)),
+           "lr_workspace_size_batch")
+    return n.value
+
+
+def lr_workspace_size_refs(ctx, views, bin_refs: int) -> int:
+    arr = (lr_view * len(views))(*views)
+    n = ctypes.c_size_t()
+    _check(ctx, load().lr_workspace_size_refs(ctx, len(views), arr, bin_refs, ctypes.byref(n)),
+           "lr_workspace_size_refs")
+    return n.value
+
+
+def lr_render(ctx, quads: lr_quads, camera: lr_camera, width: int, height: int, out_rgba: int,
+              workspace: int, workspace_bytes: int, stream: int):
+    _check(ctx, load().lr_render(ctx, ctypes.byref(quads), ctypes.byref(camera), width, height,
+                                 out_rgba, workspace, workspace_bytes, stream), "lr_render")
+
+
+def lr_render_batch(ctx, views, workspace: int, workspace_bytes: int, stream: int):
+    arr = (lr_view * len(views))(*views)
+    _check(ctx, load().lr_render_batch(ctx, len(views), arr, workspace, workspace_bytes, stream),
+           "lr_render_batch")
+
+
+def lr_render_backward(ctx, quads: lr_quads, camera: lr_camera, width: int, height: int,
+                       fwd_rgba: int, grad_out: int, grad_colors: int, workspace: int,
+                       workspace_bytes: int, stream: int):
+    _check(ctx, load().lr_render_backward(ctx, ctypes.byref(quads), ctypes.byref(camera), width,
+                                          height, fwd_rgba, grad_out, grad_colors, workspace,
+                                          workspace_bytes, stream), "lr_render_backward")
+
+
+def lr_workspace_layout(ctx, views, workspace_bytes: int) -> lr_ws_layout:
+    arr = (lr_view * len(views))(*views)
+    out = lr_ws_layout()
+    _check(ctx, load().lr_workspace_layout(ctx, len(views), arr, workspace_bytes, ctypes.byref(out)),
+           "lr_workspace_layout")
+    return out
+
+
+def lr_get_stats(ctx, raise_on_error: bool = True) -> lr_stats:
+    st = lr_stats()
+    status = load().lr_get_stats(ctx, ctypes.byref(st))
+    if raise_on_error:
+        _check(ctx, status, "lr_get_stats")
+    return st
+
+
+def lr_last_error(ctx) -> str:
+    return (load().lr_last_error(ctx) or b"").decode(errors="replace")

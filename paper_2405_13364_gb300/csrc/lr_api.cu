@@ -1,0 +1,545 @@
+// lr_api.cu -- the C ABI (include/lr.h): argument checking, workspace layout, and the
+// launch sequence of one render:
+//
+//   k_write_views  view descriptors -> workspace (kernel parameters, no host buffer)
+//   k_init         zero control block and bin counters
+//   k_setup        Stage 1  (Sec. 2, "Stage 1: quad setup")
+//   k_bin_count    Stage 2, Phase 1
+//   k_bin_scan     Stage 2, Phase 2
+//   k_bin_scatter  Stage 2, Phase 3
+//   k_bin_sort     Stage 3, Phase 2's depth sort of each bin's references (stage 1 of 2)
+//   k_raster       Stage 3: coverage, per-pixel sorter (stage 2 of 2), blending
+//   k_overflow     exact full sort of the pixels the sorter flagged
+//
+// Every grid size depends only on host-known sizes (quads, bins, SM count); all
+// data-dependent sizes are read on the device, so the sequence has no host round trip
+// and can be captured into a CUDA graph.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lr_common.cuh"
+#include "lr_raster.cuh"
+
+namespace lr {
+__global__ void k_init(Ws ws, unsigned long long refs_cap);
+__global__ void k_setup(Ws ws);
+__global__ void k_bin_count(Ws ws);
+__global__ void k_bin_scan(Ws ws);
+__global__ void k_bin_scatter(Ws ws);
+__global__ void k_bin_sort(Ws ws);
+cudaError_t overflow_occupancy(int* blocks_per_sm);
+cudaError_t launch_overflow(bool bwd, const Ws& ws, int grid, cudaStream_t st);
+
+#define LR_DECLARE_RASTER(KK)                                                       \
+  cudaError_t prepare_raster_##KK(int* blocks_flat, int* blocks_vtx, int* blocks_bwd); \
+  cudaError_t launch_raster_##KK(int mode, const Ws& ws, int grid, cudaStream_t st);
+LR_DECLARE_RASTER(1)
+LR_DECLARE_RASTER(2)
+LR_DECLARE_RASTER(3)
+LR_DECLARE_RASTER(4)
+LR_DECLARE_RASTER(6)
+LR_DECLARE_RASTER(8)
+LR_DECLARE_RASTER(12)
+
+constexpr int kViewsPerLaunch = 16;
+struct ViewChunk {
+  ViewDev v[kViewsPerLaunch];
+  int first, count;
+};
+
+__global__ void k_write_views(ViewChunk chunk, ViewDev* dst) {
+  const int i = threadIdx.x;
+  if (i < chunk.count) dst[chunk.first + i] = chunk.v[i];
+}
+
+typedef cudaError_t (*PrepareFn)(int*, int*, int*);
+typedef cudaError_t (*LaunchFn)(int, const Ws&, int, cudaStream_t);   // mode 0 flat, 1 colours, 2 backward
+
+struct RasterVariant {
+  int k;
+  PrepareFn prepare;
+  LaunchFn launch;
+};
+
+static const RasterVariant kVariants[] = {
+    {1, prepare_raster_1, launch_raster_1},   {2, prepare_raster_2, launch_raster_2},
+    {3, prepare_raster_3, launch_raster_3},   {4, prepare_raster_4, launch_raster_4},
+    {6, prepare_raster_6, launch_raster_6},   {8, prepare_raster_8, launch_raster_8},
+    {12, prepare_raster_12, launch_raster_12},
+};
+
+struct Layout {
+  size_t ctrl, views, rec_xy, rec_q, rec_rect, rec_info, bin_count, bin_off, bin_cursor, bin_order;
+  size_t refs, refs_tmp, ovf_list, total;
+  long long total_quads = 0, total_pix = 0, refs_cap = 0;
+  int total_bins = 0, total_chunks = 0;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Workspace layout. The two bin-reference arrays come last; their capacity is whatever the
+// workspace holds beyond the fixed part (set_capacity), so a caller that hit
+// LR_ERR_OVERFLOW can pass a larger workspace without recreating the context.
+static Layout make_layout(int n, const long long* Q, const int* W, const int* H) {
+  Layout L;
+  for (int i = 0; i < n; ++i) {
+    const int nbx = (W[i] + kBin - 1) / kBin, nby = (H[i] + kBin - 1) / kBin;
+    L.total_quads += Q[i];
+    L.total_pix += (long long)W[i] * H[i];
+    L.total_bins += nbx * nby;
+    L.total_chunks += (int)((Q[i] + kChunkQuads - 1) / kChunkQuads);
+  }
+  size_t o = 0;
+  auto take = [&](size_t bytes) { const size_t at = o; o = align256(o + bytes); return at; };
+  L.ctrl = take(sizeof(Ctrl));
+  L.views = take(sizeof(ViewDev) * (size_t)n);
+  L.rec_xy = take(sizeof(int4) * 2 * (size_t)L.total_quads);
+  L.rec_q = take(sizeof(float4) * (size_t)L.total_quads);
+  L.rec_rect = take(sizeof(uint2) * (size_t)L.total_quads);
+  L.rec_info = take(sizeof(uint32_t) * (size_t)L.total_quads);
+  L.bin_count = take(sizeof(uint32_t) * (size_t)L.total_bins);
+  L.bin_off = take(sizeof(uint32_t) * ((size_t)L.total_bins + 1));
+  L.bin_cursor = take(sizeof(uint32_t) * (size_t)L.total_bins);
+  L.bin_order = take(sizeof(uint32_t) * (size_t)L.total_bins);
+  L.ovf_list = take(sizeof(uint32_t) * (size_t)L.total_pix);
+  L.refs = o;      // refs and refs_tmp follow; see set_capacity
+  L.total = o;
+  return L;
+}
+
+static const long long kMaxRefs = 0xFFFFFF00LL;   // offsets are 32-bit
+
+static long long default_refs(const Layout& L, int ref_factor) {
+  return std::min((long long)ref_factor * L.total_quads + 64LL * L.total_bins + 1024, kMaxRefs);
+}
+
+static size_t bytes_for_refs(const Layout& L, long long refs) {
+  return L.refs + align256(sizeof(unsigned long long) * (size_t)refs) * 2;
+}
+
+// capacity from the bytes available, placing refs_tmp after refs
+static void set_capacity(Layout& L, size_t ws_bytes) {
+  long long cap = 0;
+  if (ws_bytes > L.refs) cap = (long long)((ws_bytes - L.refs) / (2 * sizeof(unsigned long long)));
+  cap = std::min(cap, kMaxRefs);
+  cap &= ~31LL;
+  while (cap > 0 && bytes_for_refs(L, cap) > ws_bytes) cap -= 32;
+  L.refs_cap = std::max(cap, 0LL);
+  L.refs_tmp = L.refs + align256(sizeof(unsigned long long) * (size_t)L.refs_cap);
+  L.total = bytes_for_refs(L, L.refs_cap);
+}
+
+static Ws make_ws(const Layout& L, void* base, int n_views) {
+  char* b = static_cast<char*>(base);
+  Ws w;
+  memset(&w, 0, sizeof(w));
+  w.ctrl = reinterpret_cast<Ctrl*>(b + L.ctrl);
+  w.views = reinterpret_cast<const ViewDev*>(b + L.views);
+  w.n_views = n_views;
+  w.total_bins = L.total_bins;
+  w.total_quads = L.total_quads;
+  w.total_pix = L.total_pix;
+  w.refs_cap = L.refs_cap;
+  w.rec_xy = reinterpret_cast<int4*>(b + L.rec_xy);
+  w.rec_q = reinterpret_cast<float4*>(b + L.rec_q);
+  w.rec_rect = reinterpret_cast<uint2*>(b + L.rec_rect);
+  w.rec_info = reinterpret_cast<uint32_t*>(b + L.rec_info);
+  w.bin_count = reinterpret_cast<uint32_t*>(b + L.bin_count);
+  w.bin_off = reinterpret_cast<uint32_t*>(b + L.bin_off);
+  w.bin_cursor = reinterpret_cast<uint32_t*>(b + L.bin_cursor);
+  w.bin_order = reinterpret_cast<uint32_t*>(b + L.bin_order);
+  w.refs = reinterpret_cast<unsigned long long*>(b + L.refs);
+  w.refs_tmp = reinterpret_cast<unsigned long long*>(b + L.refs_tmp);
+  w.ovf_list = reinterpret_cast<uint32_t*>(b + L.ovf_list);
+  return w;
+}
+
+}  // namespace lr
+
+using namespace lr;
+
+struct lr_ctx {
+  int device = 0;
+  int sms = 0;
+  lr_config cfg;
+  const RasterVariant* variant = nullptr;
+  int raster_blocks_flat = 1, raster_blocks_vtx = 1, raster_blocks_bwd = 1;
+  int ovf_blocks = 1;
+  // last render, for lr_get_stats
+  cudaStream_t last_stream = nullptr;
+  void* last_ws = nullptr;
+  int last_views = 0;
+  long long last_quads = 0;
+  long long last_cap = 0;
+  bool have_last = false;
+  bool last_timed = false;
+  cudaEvent_t ev[9] = {};
+  Ctrl* host_ctrl = nullptr;   // pinned
+  char err[512] = {0};
+};
+
+static lr_status fail(lr_ctx* c, lr_status s, const char* fmt, const char* detail = "") {
+  if (c) snprintf(c->err, sizeof(c->err), fmt, detail);
+  return s;
+}
+
+static lr_status cuda_fail(lr_ctx* c, cudaError_t e, const char* what) {
+  if (c) snprintf(c->err, sizeof(c->err), "%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? LR_ERR_OOM : LR_ERR_CUDA;
+}
+
+extern "C" lr_status lr_create(const lr_config* config, lr_ctx** out_ctx) {
+  if (!out_ctx) return LR_ERR_INVALID_ARG;
+  *out_ctx = nullptr;
+  lr_ctx* c = new (std::nothrow) lr_ctx();
+  if (!c) return LR_ERR_OOM;
+  memset(&c->cfg, 0, sizeof(c->cfg));
+  if (config) c->cfg = *config;
+  lr_config& g = c->cfg;
+  if (g.max_width <= 0) g.max_width = 2560;
+  if (g.max_height <= 0) g.max_height = 2048;
+  if (g.sorter_k <= 0) g.sorter_k = 3;
+  if (g.ref_factor <= 0) g.ref_factor = 4;
+  if (g.max_width > 65535 || g.max_height > 65535 || g.raster_ctas_per_sm < 0) {
+    delete c;
+    return LR_ERR_INVALID_ARG;
+  }
+  for (const auto& v : kVariants)
+    if (v.k == g.sorter_k) c->variant = &v;
+  if (!c->variant) {
+    delete c;
+    return LR_ERR_INVALID_ARG;
+  }
+  cudaError_t e;
+  if (g.device > 0) {
+    e = cudaSetDevice(g.device);
+    if (e != cudaSuccess) { delete c; return LR_ERR_CUDA; }
+  }
+  e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) e = c->variant->prepare(&c->raster_blocks_flat, &c->raster_blocks_vtx, &c->raster_blocks_bwd);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bin_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(kSortSmemCap * sizeof(unsigned long long)));
+  if (e == cudaSuccess) e = overflow_occupancy(&c->ovf_blocks);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&c->host_ctrl), sizeof(Ctrl));
+  for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev[i]);
+  if (e != cudaSuccess) {
+    lr_status s = e == cudaErrorMemoryAllocation ? LR_ERR_OOM : LR_ERR_CUDA;
+    lr_destroy(c);
+    return s;
+  }
+  if (g.raster_ctas_per_sm > 0) {
+    c->raster_blocks_flat = std::min(c->raster_blocks_flat, g.raster_ctas_per_sm);
+    c->raster_blocks_vtx = std::min(c->raster_blocks_vtx, g.raster_ctas_per_sm);
+    c->raster_blocks_bwd = std::min(c->raster_blocks_bwd, g.raster_ctas_per_sm);
+  }
+  c->raster_blocks_bwd = std::max(c->raster_blocks_bwd, 1);
+  c->raster_blocks_flat = std::max(c->raster_blocks_flat, 1);
+  c->raster_blocks_vtx = std::max(c->raster_blocks_vtx, 1);
+  c->ovf_blocks = std::max(c->ovf_blocks, 1);
+  *out_ctx = c;
+  return LR_OK;
+}
+
+extern "C" lr_status lr_destroy(lr_ctx* ctx) {
+  if (!ctx) return LR_ERR_INVALID_ARG;
+  for (int i = 0; i < 9; ++i)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  if (ctx->host_ctrl) cudaFreeHost(ctx->host_ctrl);
+  delete ctx;
+  return LR_OK;
+}
+
+static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+static lr_status check_view(lr_ctx* c, const lr_view& v) {
+  if (v.width <= 0 || v.height <= 0) return fail(c, LR_ERR_INVALID_ARG, "width and height must be positive%s");
+  if (v.width > c->cfg.max_width || v.height > c->cfg.max_height)
+    return fail(c, LR_ERR_TOO_LARGE, "resolution above the context maximum%s");
+  const lr_quads& q = v.quads;
+  if (q.num_quads < 0 || q.num_vertices < 0) return fail(c, LR_ERR_INVALID_ARG, "negative sizes%s");
+  if (q.num_quads > 0x7FFFFFFFLL / 2) return fail(c, LR_ERR_TOO_LARGE, "too many quads%s");
+  if (q.num_quads > 0) {
+    if (!q.positions || !q.colors) return fail(c, LR_ERR_INVALID_ARG, "null positions or colors%s");
+    if (!aligned(q.positions, 16) || !aligned(q.colors, 16) || (q.indices && !aligned(q.indices, 16)))
+      return fail(c, LR_ERR_INVALID_ARG, "positions, colors and indices must be 16-byte aligned%s");
+    if (q.color_mode != LR_COLOR_FLAT && q.color_mode != LR_COLOR_VERTEX)
+      return fail(c, LR_ERR_INVALID_ARG, "unknown color_mode%s");
+  }
+  if (!v.target.rgba || !aligned(v.target.rgba, 16)) return fail(c, LR_ERR_INVALID_ARG, "rgba output must be non-null and 16-byte aligned%s");
+  if ((v.target.rgba8 && !aligned(v.target.rgba8, 4)) || (v.target.frag_count && !aligned(v.target.frag_count, 4)) ||
+      (v.target.cov_hash && !aligned(v.target.cov_hash, 8)))
+    return fail(c, LR_ERR_INVALID_ARG, "misaligned optional output%s");
+  const float n = v.camera.near_z, f = v.camera.far_z;
+  if (!(n > 0.0f) || !(f >= n) || !(f < 3.4e38f)) return fail(c, LR_ERR_INVALID_ARG, "need 0 < near <= far < inf%s");
+  return LR_OK;
+}
+
+static lr_status layout_for(lr_ctx* c, int n, const lr_view* views, Layout* out) {
+  std::vector<long long> Q(n);
+  std::vector<int> W(n), H(n);
+  long long total_pix = 0;
+  for (int i = 0; i < n; ++i) {
+    Q[i] = views[i].quads.num_quads;
+    W[i] = views[i].width;
+    H[i] = views[i].height;
+    total_pix += (long long)W[i] * H[i];
+  }
+  *out = make_layout(n, Q.data(), W.data(), H.data());
+  if (out->total_quads > 0x7FFFFFFFLL || total_pix > 0xFFFFFFFFLL)
+    return fail(c, LR_ERR_TOO_LARGE, "batch too large%s");
+  return LR_OK;
+}
+
+extern "C" lr_status lr_workspace_size(const lr_ctx* ctx, int64_t num_quads, int32_t width, int32_t height,
+                                       size_t* out_bytes) {
+  if (!ctx || !out_bytes || num_quads < 0 || width <= 0 || height <= 0) return LR_ERR_INVALID_ARG;
+  if (width > ctx->cfg.max_width || height > ctx->cfg.max_height) return LR_ERR_TOO_LARGE;
+  const long long q = num_quads;
+  const int w = width, h = height;
+  Layout L = make_layout(1, &q, &w, &h);
+  *out_bytes = bytes_for_refs(L, default_refs(L, ctx->cfg.ref_factor));
+  return LR_OK;
+}
+
+extern "C" lr_status lr_workspace_size_batch(const lr_ctx* ctx, int32_t n_views, const lr_view* views,
+                                             size_t* out_bytes) {
+  return lr_workspace_size_refs(ctx, n_views, views, -1, out_bytes);
+}
+
+extern "C" lr_status lr_workspace_size_refs(const lr_ctx* ctx, int32_t n_views, const lr_view* views,
+                                            int64_t bin_refs, size_t* out_bytes) {
+  if (!ctx || !views || n_views <= 0 || !out_bytes) return LR_ERR_INVALID_ARG;
+  Layout L;
+  lr_status s = layout_for(const_cast<lr_ctx*>(ctx), n_views, views, &L);
+  if (s != LR_OK) return s;
+  if (bin_refs > kMaxRefs) return LR_ERR_TOO_LARGE;
+  const long long refs = bin_refs < 0 ? default_refs(L, ctx->cfg.ref_factor) : (long long)bin_refs;
+  *out_bytes = bytes_for_refs(L, refs);
+  return LR_OK;
+}
+
+extern "C" lr_status lr_workspace_layout(const lr_ctx* ctx, int32_t n_views, const lr_view* views,
+                                         size_t workspace_bytes, lr_ws_layout* out) {
+  if (!ctx || !views || n_views <= 0 || !out) return LR_ERR_INVALID_ARG;
+  Layout L;
+  lr_status s = layout_for(const_cast<lr_ctx*>(ctx), n_views, views, &L);
+  if (s != LR_OK) return s;
+  set_capacity(L, workspace_bytes);
+  out->rec_xy = L.rec_xy;
+  out->rec_q = L.rec_q;
+  out->rec_rect = L.rec_rect;
+  out->rec_info = L.rec_info;
+  out->bin_count = L.bin_count;
+  out->bin_off = L.bin_off;
+  out->refs = L.refs;
+  out->total_quads = L.total_quads;
+  out->total_bins = L.total_bins;
+  out->refs_capacity = L.refs_cap;
+  return LR_OK;
+}
+
+static inline void rec(lr_ctx* c, bool timed, int i, cudaStream_t s) {
+  if (timed) cudaEventRecord(c->ev[i], s);
+}
+
+struct BwdArgs {
+  const float* fwd;
+  const float* grad_out;
+  float* grad_colors;
+};
+
+static lr_status enqueue(lr_ctx* ctx, int32_t n_views, const lr_view* views, void* workspace,
+                         size_t workspace_bytes, lr_stream stream, const BwdArgs* bwd) {
+  if (!ctx) return LR_ERR_INVALID_ARG;
+  if (n_views <= 0 || !views) return fail(ctx, LR_ERR_INVALID_ARG, "need at least one view%s");
+  if (!workspace || !aligned(workspace, 256)) return fail(ctx, LR_ERR_INVALID_ARG, "workspace must be non-null and 256-byte aligned%s");
+  for (int i = 0; i < n_views; ++i) {
+    lr_status s = check_view(ctx, views[i]);
+    if (s != LR_OK) return s;
+  }
+  Layout L;
+  lr_status s = layout_for(ctx, n_views, views, &L);
+  if (s != LR_OK) return s;
+  set_capacity(L, workspace_bytes);
+  if (L.refs_cap < 1024) return fail(ctx, LR_ERR_OOM, "workspace too small (see lr_workspace_size)%s");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+
+  // ---- view descriptors ---------------------------------------------------------------
+  std::vector<ViewDev> vd(n_views);
+  long long qb = 0, pb = 0;
+  int bb = 0, cb = 0;
+  bool any_vertex = false;
+  for (int i = 0; i < n_views; ++i) {
+    const lr_view& v = views[i];
+    ViewDev& d = vd[i];
+    memset(&d, 0, sizeof(d));
+    d.pos = v.quads.positions;
+    d.idx = v.quads.indices;
+    d.col = v.quads.colors;
+    d.out = v.target.rgba;
+    d.out8 = v.target.rgba8;
+    d.cnt = v.target.frag_count;
+    d.hash = reinterpret_cast<unsigned long long*>(v.target.cov_hash);
+    const float* M = v.camera.view_proj;
+    for (int k = 0; k < 4; ++k) {
+      d.m[k] = M[k];
+      d.m[4 + k] = M[4 + k];
+      d.m[8 + k] = M[12 + k];
+    }
+    d.near_z = v.camera.near_z;
+    d.far_z = v.camera.far_z;
+    d.half_w = 0.5f * (float)v.width;
+    d.half_h = 0.5f * (float)v.height;
+    d.num_vertices = v.quads.num_vertices;
+    d.num_quads = (int)v.quads.num_quads;
+    d.color_mode = v.quads.color_mode;
+    d.width = v.width;
+    d.height = v.height;
+    d.nbx = (v.width + kBin - 1) / kBin;
+    d.nby = (v.height + kBin - 1) / kBin;
+    d.quad_base = qb;
+    d.pix_base = pb;
+    d.bin_base = bb;
+    d.chunk_base = cb;
+    qb += v.quads.num_quads;
+    pb += (long long)v.width * v.height;
+    bb += d.nbx * d.nby;
+    cb += (int)((v.quads.num_quads + kChunkQuads - 1) / kChunkQuads);
+    any_vertex |= (v.quads.color_mode == LR_COLOR_VERTEX && v.quads.num_quads > 0);
+  }
+  Ws ws = make_ws(L, workspace, n_views);
+  if (bwd) {
+    ws.fwd = bwd->fwd;
+    ws.grad_out = bwd->grad_out;
+    ws.grad_col = bwd->grad_colors;
+  }
+  ViewDev* views_dev = reinterpret_cast<ViewDev*>(static_cast<char*>(workspace) + L.views);
+  const bool timed = (ctx->cfg.flags & LR_FLAG_TIMING) != 0;
+  rec(ctx, timed, 0, st);
+  for (int first = 0; first < n_views; first += kViewsPerLaunch) {
+    ViewChunk chunk;
+    memset(&chunk, 0, sizeof(chunk));
+    chunk.first = first;
+    chunk.count = std::min(kViewsPerLaunch, n_views - first);
+    for (int i = 0; i < chunk.count; ++i) chunk.v[i] = vd[first + i];
+    k_write_views<<<1, 32, 0, st>>>(chunk, views_dev);
+  }
+  k_init<<<std::max(1, (L.total_bins + 255) / 256), 256, 0, st>>>(ws, (unsigned long long)L.refs_cap);
+  if (L.total_quads > 0) k_setup<<<(unsigned)((L.total_quads + 255) / 256), 256, 0, st>>>(ws);
+  rec(ctx, timed, 1, st);
+  if (L.total_chunks > 0) k_bin_count<<<L.total_chunks, 512, 0, st>>>(ws);
+  rec(ctx, timed, 2, st);
+  k_bin_scan<<<1, 1024, 0, st>>>(ws);
+  rec(ctx, timed, 3, st);
+  if (L.total_chunks > 0) k_bin_scatter<<<L.total_chunks, 512, 0, st>>>(ws);
+  rec(ctx, timed, 4, st);
+  k_bin_sort<<<L.total_bins, 256, kSortSmemCap * sizeof(unsigned long long), st>>>(ws);
+  rec(ctx, timed, 5, st);
+  const int mode = bwd ? 2 : (any_vertex ? 1 : 0);
+  const int rblocks = bwd ? ctx->raster_blocks_bwd : (any_vertex ? ctx->raster_blocks_vtx : ctx->raster_blocks_flat);
+  e = ctx->variant->launch(mode, ws, ctx->sms * rblocks, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "raster launch");
+  rec(ctx, timed, 6, st);
+  e = launch_overflow(bwd != nullptr, ws, ctx->sms * ctx->ovf_blocks, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "overflow launch");
+  rec(ctx, timed, 7, st);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+  ctx->last_stream = st;
+  ctx->last_ws = workspace;
+  ctx->last_views = n_views;
+  ctx->last_quads = L.total_quads;
+  ctx->last_cap = L.refs_cap;
+  ctx->have_last = true;
+  ctx->last_timed = timed;
+  return LR_OK;
+}
+
+extern "C" lr_status lr_render_batch(lr_ctx* ctx, int32_t n_views, const lr_view* views, void* workspace,
+                                     size_t workspace_bytes, lr_stream stream) {
+  return enqueue(ctx, n_views, views, workspace, workspace_bytes, stream, nullptr);
+}
+
+extern "C" lr_status lr_render_backward(lr_ctx* ctx, const lr_quads* quads, const lr_camera* camera,
+                                        int32_t width, int32_t height, const float* fwd_rgba,
+                                        const float* grad_out, float* grad_colors, void* workspace,
+                                        size_t workspace_bytes, lr_stream stream) {
+  if (!ctx) return LR_ERR_INVALID_ARG;
+  if (!quads || !camera || !fwd_rgba || !grad_out || !grad_colors)
+    return fail(ctx, LR_ERR_INVALID_ARG, "null argument%s");
+  if (quads->num_quads > 0 && quads->color_mode != LR_COLOR_FLAT)
+    return fail(ctx, LR_ERR_UNSUPPORTED, "the backward pass supports flat per-quad colours only%s");
+  if (!aligned(fwd_rgba, 16) || !aligned(grad_out, 16) || !aligned(grad_colors, 16))
+    return fail(ctx, LR_ERR_INVALID_ARG, "fwd_rgba, grad_out and grad_colors must be 16-byte aligned%s");
+  lr_view v;
+  memset(&v, 0, sizeof(v));
+  v.quads = *quads;
+  v.camera = *camera;
+  v.width = width;
+  v.height = height;
+  v.target.rgba = const_cast<float*>(fwd_rgba);   // not written by the backward pass
+  BwdArgs b{fwd_rgba, grad_out, grad_colors};
+  return enqueue(ctx, 1, &v, workspace, workspace_bytes, stream, &b);
+}
+
+extern "C" lr_status lr_render(lr_ctx* ctx, const lr_quads* quads, const lr_camera* camera, int32_t width,
+                               int32_t height, float* out_rgba, void* workspace, size_t workspace_bytes,
+                               lr_stream stream) {
+  if (!ctx) return LR_ERR_INVALID_ARG;
+  if (!quads || !camera) return fail(ctx, LR_ERR_INVALID_ARG, "null quads or camera%s");
+  lr_view v;
+  memset(&v, 0, sizeof(v));
+  v.quads = *quads;
+  v.camera = *camera;
+  v.width = width;
+  v.height = height;
+  v.target.rgba = out_rgba;
+  return lr_render_batch(ctx, 1, &v, workspace, workspace_bytes, stream);
+}
+
+extern "C" lr_status lr_get_stats(lr_ctx* ctx, lr_stats* stats) {
+  if (!ctx) return LR_ERR_INVALID_ARG;
+  if (!ctx->have_last) return fail(ctx, LR_ERR_INVALID_ARG, "no render issued on this context%s");
+  cudaError_t e = cudaStreamSynchronize(ctx->last_stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+  e = cudaMemcpy(ctx->host_ctrl, ctx->last_ws, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy(ctrl)");
+  const Ctrl& h = *ctx->host_ctrl;
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->status = h.error;
+    stats->n_views = ctx->last_views;
+    stats->quads_in = ctx->last_quads;
+    stats->quads_visible = (int64_t)h.visible;
+    for (int i = 0; i < 8; ++i) stats->culled[i] = (int64_t)h.culled[i];
+    stats->bin_refs = (int64_t)h.refs_total;
+    stats->bin_refs_capacity = ctx->last_cap;
+    stats->bins_nonempty = (int64_t)h.bins_nonempty;
+    stats->bins_high = (int64_t)h.bins_high;
+    stats->max_bin_refs = (int64_t)h.max_bin;
+    stats->fragments = (int64_t)h.fragments;
+    stats->overflow_pixels = (int64_t)h.ovf_count;
+    if (ctx->last_timed) {
+      for (int i = 0; i < 7; ++i) cudaEventElapsedTime(&stats->stage_ms[i], ctx->ev[i], ctx->ev[i + 1]);
+      cudaEventElapsedTime(&stats->stage_ms[7], ctx->ev[0], ctx->ev[7]);
+    }
+  }
+  if (h.error != 0) {
+    snprintf(ctx->err, sizeof(ctx->err), "device reported status %d (%s)", h.error,
+             h.error == LR_ERR_OVERFLOW ? "bin-reference capacity exceeded"
+                                        : h.error == LR_ERR_INVALID_ARG ? "vertex index out of range" : "error");
+    return (lr_status)h.error;
+  }
+  return LR_OK;
+}
+
+extern "C" const char* lr_last_error(const lr_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err;
+}

@@ -1,0 +1,346 @@
+// lr_bin.cu -- Stage 2 of the pipeline, quad binning (Sec. 2, "Stage 2: quad binning"),
+// plus the per-bin depth sort that feeds Stage 3.
+//
+//   k_bin_count    Phase 1: per-bin reference counts. Each CTA owns a chunk of 4096 quads
+//                  of one view and counts into shared-memory bin counters (the paper's
+//                  5120-entry arrays), then adds its non-zero counters to global memory.
+//                  Small quads (bin rectangle <= 2x2) are counted from their AABB; large
+//                  quads are tested bin by bin with a conservative per-triangle edge test
+//                  (trivial reject), the whole warp sharing one large quad's bins.
+//   k_bin_scan     Phase 2: exclusive scan of the counts into list offsets, capacity
+//                  check, and a categorisation of bins by size (the paper's empty / low /
+//                  high) that orders the rasteriser's work queue, largest bins first.
+//   k_bin_scatter  Phase 3: recomputes the chunk's counters, reserves one range per
+//                  (chunk, bin) with a global atomic, then places references with shared
+//                  memory atomics. A reference is a 64-bit sort key:
+//                  (~representative 1/w) << 32 | ~record index.
+//   k_bin_sort     Stage-1 depth sort: sorts each bin's references ascending, i.e. front
+//                  to back by a representative depth, ties with the higher quad index
+//                  first. Bins of up to 4096 references are sorted in shared memory; larger
+//                  (high-density) bins sort 4096-reference runs in shared memory and merge
+//                  them through a global buffer.
+#include "lr_common.cuh"
+
+namespace lr {
+
+// Conservative test whether a triangle of a quad can cover a pixel centre of bin (bx, by):
+// false only if one edge is negative (after the fill-rule bias) at all four corner pixel
+// centres of the bin rectangle clipped to the triangle's pixel AABB and the screen.
+__device__ bool tri_may_touch_bin(const int X[4], const int Y[4], int t, int bx, int by, int W, int H) {
+  int a = 0, b = t == 0 ? 1 : 2, c = t == 0 ? 2 : 3;
+  long long A = area2(X[a], Y[a], X[b], Y[b], X[c], Y[c]);
+  if (A == 0) return false;
+  if (A < 0) { int tmp = b; b = c; c = tmp; }
+  const int vx[3] = {X[a], X[b], X[c]}, vy[3] = {Y[a], Y[b], Y[c]};
+  const int xmin = min(vx[0], min(vx[1], vx[2])), xmax = max(vx[0], max(vx[1], vx[2]));
+  const int ymin = min(vy[0], min(vy[1], vy[2])), ymax = max(vy[0], max(vy[1], vy[2]));
+  const int x0 = max(max(ceil_div256((long long)xmin - 128), 0), bx << kBinLog2);
+  const int x1 = min(min(floor_div256((long long)xmax - 128), W - 1), (bx << kBinLog2) + kBin - 1);
+  const int y0 = max(max(ceil_div256((long long)ymin - 128), 0), by << kBinLog2);
+  const int y1 = min(min(floor_div256((long long)ymax - 128), H - 1), (by << kBinLog2) + kBin - 1);
+  if (x0 > x1 || y0 > y1) return false;
+  const long long cx[2] = {256LL * x0 + 128, 256LL * x1 + 128};
+  const long long cy[2] = {256LL * y0 + 128, 256LL * y1 + 128};
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int u = e == 0 ? 1 : (e == 1 ? 2 : 0);
+    const int w = e == 0 ? 2 : (e == 1 ? 0 : 1);
+    const long long dx = (long long)vx[w] - vx[u], dy = (long long)vy[w] - vy[u];
+    const long long bias = (dy < 0 || (dy == 0 && dx > 0)) ? 0 : -1;
+    bool all_out = true;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const long long ev = dx * (cy[i >> 1] - vy[u]) - dy * (cx[i & 1] - vx[u]) + bias;
+      all_out &= ev < 0;
+    }
+    if (all_out) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ bool quad_may_touch_bin(const Ws& ws, long long q, uint32_t info, int bx,
+                                                   int by, int W, int H) {
+  const int4 a = ws.rec_xy[2 * q], b = ws.rec_xy[2 * q + 1];
+  const int X[4] = {a.x, a.z, b.x, b.z}, Y[4] = {a.y, a.w, b.y, b.w};
+  return ((info & kInfoTri0) && tri_may_touch_bin(X, Y, 0, bx, by, W, H)) ||
+         ((info & kInfoTri1) && tri_may_touch_bin(X, Y, 1, bx, by, W, H));
+}
+
+// Representative depth of a quad inside a bin: the plane of one triangle evaluated (in
+// plain fp32, approximately) at the centre of the quad's pixel AABB clipped to the bin,
+// clamped to the range of the quad's vertex 1/w. Only the order quality of stage 1
+// depends on it; exactness is restored by the per-pixel sorter and the overflow path.
+__device__ __forceinline__ float rep_depth(const Ws& ws, long long q, uint32_t info, int x0, int x1,
+                                           int y0, int y1) {
+  const int4 a = ws.rec_xy[2 * q], b = ws.rec_xy[2 * q + 1];
+  const float4 qq = ws.rec_q[q];
+  const float Xs[4] = {(float)a.x, (float)a.z, (float)b.x, (float)b.z};
+  const float Ys[4] = {(float)a.y, (float)a.w, (float)b.y, (float)b.w};
+  const float Q[4] = {qq.x, qq.y, qq.z, qq.w};
+  const float qmin = fminf(fminf(Q[0], Q[1]), fminf(Q[2], Q[3]));
+  const float qmax = fmaxf(fmaxf(Q[0], Q[1]), fmaxf(Q[2], Q[3]));
+  const int i1 = (info & kInfoTri0) ? 1 : 2, i2 = (info & kInfoTri0) ? 2 : 3;
+  const float px = 128.0f * (float)(x0 + x1) + 128.0f, py = 128.0f * (float)(y0 + y1) + 128.0f;
+  const float A = (Xs[i1] - Xs[0]) * (Ys[i2] - Ys[0]) - (Ys[i1] - Ys[0]) * (Xs[i2] - Xs[0]);
+  if (!(fabsf(A) > 0.0f)) return qmax;
+  const float l1 = ((Xs[0] - Xs[i2]) * (py - Ys[i2]) - (Ys[0] - Ys[i2]) * (px - Xs[i2])) / A;
+  const float l2 = ((Xs[i1] - Xs[0]) * (py - Ys[0]) - (Ys[i1] - Ys[0]) * (px - Xs[0])) / A;
+  float r = Q[0] + l1 * (Q[i1] - Q[0]) + l2 * (Q[i2] - Q[0]);
+  r = fminf(fmaxf(r, qmin), qmax);
+  return r > 0.0f ? r : qmin;
+}
+
+__device__ __forceinline__ unsigned long long ref_key(float rep, long long q) {
+  return ((unsigned long long)(~__float_as_uint(rep)) << 32) | (unsigned long long)(~(uint32_t)q);
+}
+
+// Shared by count and scatter: for each (visible quad, touched bin) of the CTA's chunk
+// call f(q, local_bin, bx, by). Small quads enumerate their AABB bins in their own
+// thread; large quads are processed by the whole warp, one bin per lane.
+template <typename F>
+__device__ __forceinline__ void for_each_ref(const Ws& ws, const ViewDev& V, long long q0, long long q1,
+                                             F&& f) {
+  const int lane = threadIdx.x & 31;
+  for (long long base = q0 + (threadIdx.x & ~31); base < q1; base += blockDim.x) {
+    const long long q = base + lane;
+    const bool in = q < q1;
+    uint2 rect = make_uint2(kRectInvisible, kRectInvisible);
+    uint32_t info = 0;
+    if (in) { rect = ws.rec_rect[q]; info = ws.rec_info[q]; }
+    const bool vis = in && rect.x != kRectInvisible;
+    const int px0 = rect.x & 0xffff, px1 = rect.x >> 16, py0 = rect.y & 0xffff, py1 = rect.y >> 16;
+    if (vis && !(info & kInfoLarge)) {
+      for (int by = py0 >> kBinLog2; by <= (py1 >> kBinLog2); ++by)
+        for (int bx = px0 >> kBinLog2; bx <= (px1 >> kBinLog2); ++bx) f(q, by * V.nbx + bx, bx, by, rect, info);
+    }
+    unsigned large = __ballot_sync(0xffffffffu, vis && (info & kInfoLarge));
+    while (large) {
+      const int src = __ffs(large) - 1;
+      large &= large - 1;
+      const long long lq = __shfl_sync(0xffffffffu, q, src);
+      const uint2 lr = make_uint2(__shfl_sync(0xffffffffu, rect.x, src), __shfl_sync(0xffffffffu, rect.y, src));
+      const uint32_t li = __shfl_sync(0xffffffffu, info, src);
+      const int bx0 = (lr.x & 0xffff) >> kBinLog2, bx1 = (lr.x >> 16) >> kBinLog2;
+      const int by0 = (lr.y & 0xffff) >> kBinLog2, by1 = (lr.y >> 16) >> kBinLog2;
+      const int bw = bx1 - bx0 + 1, nb = bw * (by1 - by0 + 1);
+      for (int i = lane; i < nb; i += 32) {
+        const int bx = bx0 + i % bw, by = by0 + i / bw;
+        if (quad_may_touch_bin(ws, lq, li, bx, by, V.width, V.height)) f(lq, by * V.nbx + bx, bx, by, lr, li);
+      }
+    }
+  }
+}
+
+__global__ __launch_bounds__(512) void k_bin_count(Ws ws) {
+  __shared__ uint32_t hist[kHistSmemBins];
+  const int v = view_of_chunk(ws.views, ws.n_views, blockIdx.x);
+  const ViewDev& V = ws.views[v];
+  const long long q0 = V.quad_base + (long long)(blockIdx.x - V.chunk_base) * kChunkQuads;
+  const long long q1 = min(q0 + kChunkQuads, V.quad_base + V.num_quads);
+  const int nb = V.nbx * V.nby;
+  const bool smem = nb <= kHistSmemBins;
+  if (smem)
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0u;
+  __syncthreads();
+  for_each_ref(ws, V, q0, q1, [&](long long, int b, int, int, uint2, uint32_t) {
+    if (smem) atomicAdd(&hist[b], 1u);
+    else atomicAdd(&ws.bin_count[V.bin_base + b], 1u);
+  });
+  __syncthreads();
+  if (smem)
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+      if (hist[b]) atomicAdd(&ws.bin_count[V.bin_base + b], hist[b]);
+}
+
+// Single CTA. Offsets (exclusive scan), capacity check, and the bin order for the
+// rasteriser: bins by decreasing size class (floor(log2(count)) + 1), empty bins last.
+__global__ __launch_bounds__(1024) void k_bin_scan(Ws ws) {
+  __shared__ unsigned long long warp_sums[32];
+  __shared__ uint32_t cls_count[34];
+  __shared__ uint32_t cls_base[34];
+  __shared__ unsigned long long carry;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int n = ws.total_bins;
+  if (tid < 34) cls_count[tid] = 0;
+  if (tid == 0) carry = 0;
+  __syncthreads();
+  unsigned long long nonempty = 0, high = 0, mx = 0;
+  for (int base = 0; base < n; base += 1024) {
+    const int i = base + tid;
+    const uint32_t c = i < n ? ws.bin_count[i] : 0u;
+    if (i < n) {
+      nonempty += c > 0;
+      high += c > (uint32_t)kSortSmemCap;
+      mx = c > mx ? c : mx;
+      atomicAdd(&cls_count[c ? 33 - __clz(c) : 0], 1u);
+    }
+    unsigned long long x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      unsigned long long s = warp_sums[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += y;
+      }
+      warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const unsigned long long incl = x + (wid ? warp_sums[wid - 1] : 0ull) + carry;
+    if (i < n) {
+      const unsigned long long excl = incl - c;
+      ws.bin_off[i] = (uint32_t)min(excl, (unsigned long long)ws.refs_cap);
+      ws.bin_cursor[i] = (uint32_t)min(excl, (unsigned long long)ws.refs_cap);
+    }
+    __syncthreads();
+    if (tid == 1023) carry = incl;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    ws.bin_off[n] = (uint32_t)min(carry, (unsigned long long)ws.refs_cap);
+    ws.ctrl->refs_total = carry;
+    ws.ctrl->raster_items = (unsigned long long)n * kHbPerBin;
+    if (carry > (unsigned long long)ws.refs_cap) set_error(ws.ctrl, LR_ERR_OVERFLOW);
+  }
+  // statistics
+  for (int o = 16; o > 0; o >>= 1) {
+    nonempty += __shfl_xor_sync(0xffffffffu, nonempty, o);
+    high += __shfl_xor_sync(0xffffffffu, high, o);
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  if (lane == 0) {
+    atomicAdd(&ws.ctrl->bins_nonempty, nonempty);
+    atomicAdd(&ws.ctrl->bins_high, high);
+    atomicMax(&ws.ctrl->max_bin, mx);
+  }
+  __syncthreads();
+  // class bases, largest class first
+  if (tid == 0) {
+    uint32_t s = 0;
+    for (int k = 33; k >= 0; --k) { cls_base[k] = s; s += cls_count[k]; }
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += 1024) {
+    const uint32_t c = ws.bin_count[i];
+    const uint32_t pos = atomicAdd(&cls_base[c ? 33 - __clz(c) : 0], 1u);
+    ws.bin_order[pos] = (uint32_t)i;
+  }
+}
+
+__global__ __launch_bounds__(512) void k_bin_scatter(Ws ws) {
+  __shared__ uint32_t hist[kHistSmemBins];
+  if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
+  const int v = view_of_chunk(ws.views, ws.n_views, blockIdx.x);
+  const ViewDev& V = ws.views[v];
+  const long long q0 = V.quad_base + (long long)(blockIdx.x - V.chunk_base) * kChunkQuads;
+  const long long q1 = min(q0 + kChunkQuads, V.quad_base + V.num_quads);
+  const int nb = V.nbx * V.nby;
+  const bool smem = nb <= kHistSmemBins;
+  if (smem) {
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0u;
+    __syncthreads();
+    for_each_ref(ws, V, q0, q1, [&](long long, int b, int, int, uint2, uint32_t) { atomicAdd(&hist[b], 1u); });
+    __syncthreads();
+    // reserve one contiguous range per touched bin
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+      if (hist[b]) hist[b] = atomicAdd(&ws.bin_cursor[V.bin_base + b], hist[b]);
+    __syncthreads();
+  }
+  for_each_ref(ws, V, q0, q1, [&](long long q, int b, int bx, int by, uint2 rect, uint32_t info) {
+    const uint32_t slot = smem ? atomicAdd(&hist[b], 1u) : atomicAdd(&ws.bin_cursor[V.bin_base + b], 1u);
+    const int x0 = max((int)(rect.x & 0xffff), bx << kBinLog2);
+    const int x1 = min((int)(rect.x >> 16), (bx << kBinLog2) + kBin - 1);
+    const int y0 = max((int)(rect.y & 0xffff), by << kBinLog2);
+    const int y1 = min((int)(rect.y >> 16), (by << kBinLog2) + kBin - 1);
+    if (slot < (uint32_t)ws.refs_cap) ws.refs[slot] = ref_key(rep_depth(ws, q, info, x0, x1, y0, y1), q);
+  });
+}
+
+// ---- per-bin sort --------------------------------------------------------------------
+
+__device__ void smem_bitonic_sort(unsigned long long* s, int n2) {
+  // ascending bitonic sort of s[0, n2), n2 a power of two, by the whole CTA
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < (n2 >> 1); i += blockDim.x) {
+        const int lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+        const int hi = lo | j;
+        const bool up = (lo & k) == 0;
+        const unsigned long long a = s[lo], b = s[hi];
+        if ((a > b) == up) { s[lo] = b; s[hi] = a; }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Merge sorted runs a[0, na) and b[0, nb) into out, split evenly over the CTA (merge path).
+__device__ void cta_merge(const unsigned long long* a, int na, const unsigned long long* b, int nb,
+                          unsigned long long* out) {
+  const int total = na + nb;
+  const int per = (total + blockDim.x - 1) / blockDim.x;
+  const int d0 = min((int)threadIdx.x * per, total), d1 = min(d0 + per, total);
+  if (d0 >= d1) return;
+  // find i + j = d0 with a[i-1] < b[j] and b[j-1] < a[i] (keys are unique)
+  int lo = max(0, d0 - nb), hi = min(d0, na);
+  while (lo < hi) {
+    const int i = (lo + hi) >> 1;
+    if (a[i] < b[d0 - i - 1]) lo = i + 1; else hi = i;
+  }
+  int i = lo, j = d0 - lo;
+  for (int d = d0; d < d1; ++d) {
+    if (j >= nb || (i < na && a[i] < b[j])) out[d] = a[i++];
+    else out[d] = b[j++];
+  }
+}
+
+__global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {
+  extern __shared__ unsigned long long sbuf[];
+  if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
+  const int bin = blockIdx.x;
+  const uint32_t off = ws.bin_off[bin];
+  const int n = (int)(ws.bin_off[bin + 1] - off);
+  if (n <= 1) return;
+  unsigned long long* r = ws.refs + off;
+  if (n <= kSortSmemCap) {
+    int n2 = 32;
+    while (n2 < n) n2 <<= 1;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) sbuf[i] = i < n ? r[i] : ~0ull;
+    __syncthreads();
+    smem_bitonic_sort(sbuf, n2);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = sbuf[i];
+    return;
+  }
+  // high-density bin: sort runs of kSortSmemCap in shared memory, then merge in global
+  for (int s = 0; s < n; s += kSortSmemCap) {
+    const int m = min(kSortSmemCap, n - s);
+    for (int i = threadIdx.x; i < kSortSmemCap; i += blockDim.x) sbuf[i] = i < m ? r[s + i] : ~0ull;
+    __syncthreads();
+    smem_bitonic_sort(sbuf, kSortSmemCap);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) r[s + i] = sbuf[i];
+    __syncthreads();
+  }
+  unsigned long long* src = r;
+  unsigned long long* dst = ws.refs_tmp + off;
+  for (int run = kSortSmemCap; run < n; run <<= 1) {
+    for (int s = 0; s < n; s += 2 * run) {
+      const int na = min(run, n - s);
+      const int nbb = min(run, max(0, n - s - run));
+      cta_merge(src + s, na, src + s + na, nbb, dst + s);
+    }
+    __syncthreads();
+    unsigned long long* t = src; src = dst; dst = t;
+  }
+  if (src != r) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = src[i];
+  }
+}
+
+}  // namespace lr

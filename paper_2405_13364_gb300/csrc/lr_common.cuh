@@ -1,0 +1,157 @@
+// lr_common.cuh -- device-side data layout shared by the pipeline kernels.
+//
+// One render processes a batch of views (a single frame is a batch of one). Every stage
+// runs as one launch over all views: quads, bins and pixels of all views live in
+// flattened index spaces, and each view's slice starts at a base offset stored in its
+// ViewDev record.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lr.h"
+
+namespace lr {
+
+constexpr int kBinLog2 = 5;                 // 32x32-pixel bins (Sec. 2, Stage 2)
+constexpr int kBin = 1 << kBinLog2;
+constexpr int kHbW = 8, kHbH = 4;           // 8x4 half-blocks (Sec. 2, Stage 3)
+constexpr int kHbPerBin = (kBin / kHbW) * (kBin / kHbH);   // 32
+constexpr float kGuardPx = 16384.0f;        // guard band, pixels
+constexpr int kSortSmemCap = 4096;          // bins up to this many refs sort in shared memory
+constexpr int kHistSmemBins = 5120;         // shared-memory bin counters per CTA (Sec. 2 Stage 2)
+constexpr int kChunkQuads = 4096;           // quads per binning CTA
+
+// cull reasons (stats and rec_info bits 8..11)
+enum Cull : uint32_t {
+  kVisible = 0, kBadIndex = 1, kNonFinite = 2, kDepth = 3, kGuard = 4, kDegenerate = 5,
+  kNoPixel = 6
+};
+
+// rec_info bits
+constexpr uint32_t kInfoTri0 = 1u;          // triangle 0 has non-zero area
+constexpr uint32_t kInfoTri1 = 2u;          // triangle 1 has non-zero area
+constexpr uint32_t kInfoLarge = 4u;         // bin rectangle larger than 2x2 bins
+constexpr uint32_t kRectInvisible = 0x0000FFFFu;   // rect.x value of a culled quad
+
+struct ViewDev {
+  const float* pos;          // f32[V][3]
+  const uint32_t* idx;       // u32[Q][4] or nullptr
+  const float* col;          // flat f32[Q][4] or vertex f32[V][4]
+  float* out;                // f32[H][W][4]
+  uint8_t* out8;             // optional
+  uint32_t* cnt;             // optional
+  unsigned long long* hash;  // optional
+  float m[12];               // rows 0, 1, 3 of the view-projection (x, y, w)
+  float near_z, far_z;
+  float half_w, half_h;
+  long long num_vertices;
+  long long quad_base;       // first record of this view in the flattened quad space
+  long long pix_base;        // first pixel of this view in the flattened pixel space
+  int num_quads;
+  int color_mode;
+  int width, height;
+  int nbx, nby;              // bins per row / column
+  int bin_base;              // first bin of this view in the flattened bin space
+  int chunk_base;            // first binning chunk (kChunkQuads quads) of this view
+};
+
+// Device control block at the start of the workspace.
+struct Ctrl {
+  int error;                         // first error (lr_status), 0 = none
+  int pad0;
+  unsigned long long refs_total;     // sum of bin counts = references needed
+  unsigned long long refs_cap;
+  unsigned long long raster_head;    // rasteriser work queue
+  unsigned long long raster_items;
+  unsigned long long ovf_count;      // pixels registered for the exact path
+  unsigned long long ovf_head;
+  unsigned long long sort_head;
+  unsigned long long fragments;
+  unsigned long long visible;
+  unsigned long long culled[8];
+  unsigned long long bins_nonempty;
+  unsigned long long bins_high;
+  unsigned long long max_bin;
+  unsigned long long pad[8];
+};
+
+// Pointers into the workspace for one render (passed by value to every kernel).
+struct Ws {
+  Ctrl* ctrl;
+  const ViewDev* views;
+  int n_views;
+  int total_bins;
+  long long total_quads;
+  long long total_pix;
+  long long refs_cap;
+  int4* rec_xy;              // [2 * total_quads]: (X0,Y0,X1,Y1), (X2,Y2,X3,Y3) 8-bit subpixel
+  float4* rec_q;             // [total_quads]: 1/w per vertex
+  uint2* rec_rect;           // [total_quads]: pixel AABB (px0 | px1 << 16, py0 | py1 << 16)
+  uint32_t* rec_info;        // [total_quads]: kInfo* bits | cull reason << 8
+  uint32_t* bin_count;       // [total_bins]
+  uint32_t* bin_off;         // [total_bins + 1]
+  uint32_t* bin_cursor;      // [total_bins]
+  uint32_t* bin_order;       // [total_bins]: bins by decreasing reference count
+  unsigned long long* refs;      // [refs_cap] sorted per bin: (~rep_bits << 32) | ~record
+  unsigned long long* refs_tmp;  // [refs_cap] merge buffer of the high-density sort
+  uint32_t* ovf_list;        // [total_pix] flattened pixel ids registered for the exact path
+  // backward
+  const float* grad_out;     // f32[H][W][4] of view 0
+  const float* fwd;          // f32[H][W][4] of view 0
+  float* grad_col;           // f32[Q][4] of view 0
+};
+
+__device__ __forceinline__ void set_error(Ctrl* c, int code) { atomicCAS(&c->error, 0, code); }
+
+// View owning a flattened quad / bin / pixel index (views are few; binary search).
+__device__ __forceinline__ int view_of_quad(const ViewDev* v, int n, long long q) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (v[mid].quad_base <= q) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ int view_of_bin(const ViewDev* v, int n, int b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (v[mid].bin_base <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ int view_of_chunk(const ViewDev* v, int n, int c) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (v[mid].chunk_base <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ int view_of_pixel(const ViewDev* v, int n, long long p) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (v[mid].pix_base <= p) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// floor(a / 256) and ceil(a / 256) for signed 64-bit a
+__device__ __forceinline__ int floor_div256(long long a) { return (int)(a >> 8); }
+__device__ __forceinline__ int ceil_div256(long long a) { return (int)(-((-a) >> 8)); }
+
+__device__ __forceinline__ long long area2(int xa, int ya, int xb, int yb, int xc, int yc) {
+  return (long long)(xb - xa) * (long long)(yc - ya) - (long long)(yb - ya) * (long long)(xc - xa);
+}
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  // splitmix64 output function (Steele, Lea, Flood 2014; constants as published by Vigna)
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+}  // namespace lr

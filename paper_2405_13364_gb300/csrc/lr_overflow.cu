@@ -1,0 +1,243 @@
+// lr_overflow.cu -- the exact fallback for pixels whose order the fixed-size per-pixel
+// sorter could not guarantee. The paper detects such pixels by growing the depth filter
+// by one and notes they "could be registered and afterwards processed by a slower,
+// conservative algorithm" (Sec. 2, "Sample blending"; Sec. 3, "Fragment sorting errors").
+//
+// One warp per registered pixel. The warp re-gathers every fragment covering the pixel
+// from its bin's reference list (exact 64-bit edge tests, the same depth key as the
+// rasteriser), sorts them fully and composites front to back. Memory is bounded: a pass
+// keeps the kOvfKeep nearest fragments below a threshold in a shared-memory buffer (when
+// the buffer fills, it is sorted and cut back to kOvfKeep), composites them, lowers the
+// threshold to the last composited key and repeats until no fragment is left. Any depth
+// complexity is handled, at one re-scan of the bin per kOvfKeep fragments.
+#include "lr_raster.cuh"
+
+namespace lr {
+
+// Exact fragment of record rec, triangle t at pixel (px, py): returns false if the pixel
+// centre is not covered; otherwise the sort key and straight RGBA colour.
+__device__ bool frag_eval(const Ws& ws, const ViewDev& V, uint32_t rec, int t, int px, int py,
+                          unsigned long long* sk, float4* col) {
+  const uint32_t info = ws.rec_info[rec];
+  if (!(info & (t ? kInfoTri1 : kInfoTri0))) return false;
+  const int4 A4 = ws.rec_xy[2ull * rec], B4 = ws.rec_xy[2ull * rec + 1];
+  const int X[4] = {A4.x, A4.z, B4.x, B4.z}, Y[4] = {A4.y, A4.w, B4.y, B4.w};
+  const float4 Qv = ws.rec_q[rec];
+  const float qv[4] = {Qv.x, Qv.y, Qv.z, Qv.w};
+  int ia = 0, ib = t ? 2 : 1, ic = t ? 3 : 2;
+  long long A = area2(X[ia], Y[ia], X[ib], Y[ib], X[ic], Y[ic]);
+  if (A < 0) { const int tmp = ib; ib = ic; ic = tmp; A = -A; }
+  const int vi[3] = {ia, ib, ic};
+  const long long Px = 256LL * px + 128, Py = 256LL * py + 128;
+  long long e[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int u = vi[k == 0 ? 1 : (k == 1 ? 2 : 0)];
+    const int w = vi[k == 0 ? 2 : (k == 1 ? 0 : 1)];
+    const long long dx = (long long)X[w] - X[u], dy = (long long)Y[w] - Y[u];
+    e[k] = dx * (Py - Y[u]) - dy * (Px - X[u]);
+    const bool owned = dy < 0 || (dy == 0 && dx > 0);
+    if (!(e[k] > 0 || (e[k] == 0 && owned))) return false;
+  }
+  const float inv = __fdiv_rn(1.0f, __ll2float_rn(A));
+  const float l1 = __fmul_rn(__ll2float_rn(e[1]), inv);
+  const float l2 = __fmul_rn(__ll2float_rn(e[2]), inv);
+  const float key = __fadd_rn(qv[ia], __fadd_rn(__fmul_rn(l1, __fsub_rn(qv[ib], qv[ia])),
+                                                 __fmul_rn(l2, __fsub_rn(qv[ic], qv[ia]))));
+  const uint32_t jl = (uint32_t)(rec - V.quad_base);
+  *sk = ((unsigned long long)__float_as_uint(key) << 32) | (2u * jl + (uint32_t)t);
+  if (col) {
+    if (V.color_mode == LR_COLOR_FLAT) {
+      *col = __ldg(reinterpret_cast<const float4*>(V.col) + jl);
+    } else {
+      uint4 q4;
+      if (V.idx) q4 = __ldg(reinterpret_cast<const uint4*>(V.idx) + jl);
+      else q4 = make_uint4(4 * jl, 4 * jl + 1, 4 * jl + 2, 4 * jl + 3);
+      const uint32_t vids[4] = {q4.x, q4.y, q4.z, q4.w};
+      const float l0 = __fmul_rn(__ll2float_rn(e[0]), inv);
+      const float ls[3] = {l0, l1, l2};
+      float4 num = make_float4(0.f, 0.f, 0.f, 0.f);
+      float den = 0.f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float wk = ls[k] * qv[vi[k]];
+        const float4 c = __ldg(reinterpret_cast<const float4*>(V.col) + vids[vi[k]]);
+        num.x += wk * c.x; num.y += wk * c.y; num.z += wk * c.z; num.w += wk * c.w;
+        den += wk;
+      }
+      const float r = 1.0f / den;
+      *col = make_float4(num.x * r, num.y * r, num.z * r, num.w * r);
+    }
+  }
+  return true;
+}
+
+// descending bitonic sort of buf[0, n2) by one warp (n2 a power of two >= 32)
+__device__ void warp_sort_desc(unsigned long long* buf, int n2) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < (n2 >> 1); i += 32) {
+        const int lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+        const int hi = lo | j;
+        const bool down = (lo & k) == 0;
+        const unsigned long long a = buf[lo], b = buf[hi];
+        if ((a < b) == down) { buf[lo] = b; buf[hi] = a; }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+__device__ __forceinline__ int pow2_at_least(int n) {
+  int p = 32;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+// BWD: instead of writing the pixel, accumulate the gradient of the flat per-quad RGBA
+// (same formulas as the rasteriser's backward), with each lane walking its segment of the
+// sorted fragments from the exact prefix (colour, transmittance) of the lanes before it.
+template <bool BWD>
+__global__ __launch_bounds__(kOvfThreads) void k_overflow(Ws ws) {
+  __shared__ unsigned long long sbuf[kOvfThreads / 32][kOvfBuf];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long* buf = sbuf[warp];
+  if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
+  const unsigned long long total = ws.ctrl->ovf_count;
+  for (;;) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(&ws.ctrl->ovf_head, 1ull);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= total) break;
+    const long long pid = ws.ovf_list[item];
+    const int v = view_of_pixel(ws.views, ws.n_views, pid);
+    const ViewDev& V = ws.views[v];
+    const long long pidx = pid - V.pix_base;
+    const int px = (int)(pidx % V.width), py = (int)(pidx / V.width);
+    const int bin_g = V.bin_base + (py >> kBinLog2) * V.nbx + (px >> kBinLog2);
+    const uint32_t off = ws.bin_off[bin_g];
+    const int n = (int)(ws.bin_off[bin_g + 1] - off);
+
+    float cr = 0.f, cg = 0.f, cb = 0.f, T = 1.f;
+    unsigned long long tau = kSent;   // exclusive upper bound of the fragments still to do
+    GradPixel gp;
+    if (BWD) {
+      const float4 gq = reinterpret_cast<const float4*>(ws.grad_out)[pidx];
+      const float4 fq = reinterpret_cast<const float4*>(ws.fwd)[pidx];
+      gp.gr = gq.x; gp.gg = gq.y; gp.gb = gq.z; gp.ga = gq.w;
+      gp.fr = fq.x; gp.fg = fq.y; gp.fb = fq.z; gp.fT = 1.0f - fq.w;
+      gp.grad = ws.grad_col;
+    }
+    for (;;) {
+      int nbuf = 0, below = 0;
+      unsigned long long lb = 0;     // exclusive lower bound once the buffer was cut back
+      for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        bool hit = false;
+        uint32_t rec = 0;
+        if (i < n) {
+          rec = ~(uint32_t)ws.refs[off + i];
+          if (rec < (uint64_t)ws.total_quads) {
+            const uint2 r = ws.rec_rect[rec];
+            hit = (int)(r.x & 0xffff) <= px && (int)(r.x >> 16) >= px && (int)(r.y & 0xffff) <= py &&
+                  (int)(r.y >> 16) >= py;
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          unsigned long long sk = 0;
+          const bool cov = hit && frag_eval(ws, V, rec, t, px, py, &sk, nullptr) && sk < tau;
+          below += __popc(__ballot_sync(0xffffffffu, cov));
+          const bool keep = cov && sk > lb;
+          const unsigned m = __ballot_sync(0xffffffffu, keep);
+          if (keep) buf[nbuf + __popc(m & ((1u << lane) - 1u))] = sk;
+          nbuf += __popc(m);
+          __syncwarp();
+          if (nbuf >= kOvfBuf - 32) {
+            const int n2 = pow2_at_least(nbuf);
+            for (int k = nbuf + lane; k < n2; k += 32) buf[k] = 0ull;
+            __syncwarp();
+            warp_sort_desc(buf, n2);
+            nbuf = kOvfKeep;
+            lb = buf[kOvfKeep - 1];
+          }
+        }
+      }
+      const int n2 = pow2_at_least(nbuf);
+      for (int k = nbuf + lane; k < n2; k += 32) buf[k] = 0ull;
+      __syncwarp();
+      warp_sort_desc(buf, n2);
+      const int m = min(nbuf, kOvfKeep);
+      // composite buf[0, m) front to back: per-lane segments, then an ordered combine
+      const int seg = (m + 31) / 32;
+      float sr = 0.f, sg = 0.f, sb = 0.f, sT = 1.f;
+      for (int k = lane * seg; k < min(m, (lane + 1) * seg); ++k) {
+        const unsigned long long sk = buf[k];
+        const uint32_t id = (uint32_t)sk;
+        float4 col;
+        unsigned long long dummy;
+        frag_eval(ws, V, (uint32_t)(V.quad_base + (id >> 1)), (int)(id & 1u), px, py, &dummy, &col);
+        const float w = sT * col.w;
+        sr += w * col.x; sg += w * col.y; sb += w * col.z;
+        sT *= 1.0f - col.w;
+      }
+      // inclusive scan of (C, T) pairs with (C1, T1) o (C2, T2) = (C1 + T1 C2, T1 T2)
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float pr = __shfl_up_sync(0xffffffffu, sr, o), pg = __shfl_up_sync(0xffffffffu, sg, o);
+        const float pb = __shfl_up_sync(0xffffffffu, sb, o), pT = __shfl_up_sync(0xffffffffu, sT, o);
+        if (lane >= o) {
+          sr = pr + pT * sr; sg = pg + pT * sg; sb = pb + pT * sb; sT = pT * sT;
+        }
+      }
+      if (BWD) {
+        // exclusive prefix of this lane's segment, then walk it again with exact state
+        float er = __shfl_up_sync(0xffffffffu, sr, 1), eg = __shfl_up_sync(0xffffffffu, sg, 1);
+        float eb = __shfl_up_sync(0xffffffffu, sb, 1), eT = __shfl_up_sync(0xffffffffu, sT, 1);
+        if (lane == 0) { er = eg = eb = 0.f; eT = 1.f; }
+        float wr = cr + T * er, wg = cg + T * eg, wb = cb + T * eb, wT = T * eT;
+        for (int k = lane * seg; k < min(m, (lane + 1) * seg); ++k) {
+          const uint32_t id = (uint32_t)buf[k];
+          const uint32_t j = id >> 1;
+          const float4 col = __ldg(reinterpret_cast<const float4*>(V.col) + j);
+          const float w = wT * col.w;
+          wr += w * col.x; wg += w * col.y; wb += w * col.z;
+          const float om = 1.0f - col.w;
+          float da = gp.gr * wT * col.x + gp.gg * wT * col.y + gp.gb * wT * col.z;
+          if (om > 1e-6f) {
+            const float inv = 1.0f / om;
+            da -= (gp.gr * (gp.fr - wr) + gp.gg * (gp.fg - wg) + gp.gb * (gp.fb - wb)) * inv;
+            da += gp.ga * gp.fT * inv;
+          }
+          float* gq = gp.grad + 4ull * j;
+          atomicAdd(gq + 0, gp.gr * w);
+          atomicAdd(gq + 1, gp.gg * w);
+          atomicAdd(gq + 2, gp.gb * w);
+          atomicAdd(gq + 3, da);
+          wT *= om;
+        }
+      }
+      sr = __shfl_sync(0xffffffffu, sr, 31); sg = __shfl_sync(0xffffffffu, sg, 31);
+      sb = __shfl_sync(0xffffffffu, sb, 31); sT = __shfl_sync(0xffffffffu, sT, 31);
+      cr += T * sr; cg += T * sg; cb += T * sb; T *= sT;
+      if (below <= kOvfKeep || m == 0) break;
+      tau = buf[m - 1];
+      __syncwarp();
+    }
+    if (!BWD && lane == 0) write_pixel(V, pidx, cr, cg, cb, T);
+    __syncwarp();
+  }
+}
+
+cudaError_t overflow_occupancy(int* blocks_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_overflow<false>, kOvfThreads, 0);
+}
+
+cudaError_t launch_overflow(bool bwd, const Ws& ws, int grid, cudaStream_t st) {
+  if (bwd) k_overflow<true><<<grid, kOvfThreads, 0, st>>>(ws);
+  else k_overflow<false><<<grid, kOvfThreads, 0, st>>>(ws);
+  return cudaGetLastError();
+}
+
+}  // namespace lr

@@ -1,0 +1,473 @@
+// lr_raster.cuh -- Stage 3 of the pipeline, bin rasterisation (Sec. 2, "Stage 3: bin
+// rasterization"), with the exact fallback the paper sketches (Sec. 2, "Sample blending").
+//
+// Work decomposition. Every 32x32 bin is cut into 32 half-blocks of 8x4 pixels (the
+// paper's tri-half-block granularity). A half-block is one work item and one warp: lane
+// = pixel. Persistent warps take items from a device queue ordered by bin size (largest
+// bins first), so high-density bins are spread over many warps instead of one CTA.
+//
+// Per half-block (all from the bin's reference list, already sorted front to back by
+// k_bin_sort -- stage 1 of the two-stage sort):
+//   1. filter: 32 references at a time, test the quad's pixel AABB against the half-block,
+//      and queue the hits in shared memory (order preserved);
+//   2. triangle setup, lane-parallel: for 32 queued quads, both triangles' integer edge
+//      functions at the half-block origin, per-pixel steps, 1/area, depth-plane deltas;
+//      a triangle whose edge values stay below 2^30 on the half-block is marked "fast"
+//      and evaluated with 32-bit integers, others with exact 64-bit integers;
+//   3. coverage, warp-uniform loop over the 64 triangles: each lane tests its own pixel
+//      centre (top-left rule) and sets one bit per covering triangle;
+//   4. fragments, per lane in queue order: the exact depth key of the fragment
+//      (interpolated 1/w, identical bit for bit to the oracle's formula) is pushed into a
+//      K-slot register sorter (stage 2, the paper's "depth filter"). When full,
+//      the nearest element is evicted and blended front to back. If a fragment arrives
+//      that is nearer than the last evicted one, the stream was not in order for this
+//      pixel: the pixel is flagged and registered for k_overflow.
+// Sort keys are (float bits of key) << 32 | (2 * quad + triangle): distinct per pixel, so
+// the per-pixel order is total and the result is unique.
+#pragma once
+
+#include "lr_common.cuh"
+
+namespace lr {
+
+constexpr uint32_t kTriValid = 1u, kTriFast = 2u, kTriFlatCol = 4u;   // + corr bits 3..5
+constexpr unsigned long long kSent = ~0ull;
+constexpr int kRasterThreads = 256;
+constexpr int kRasterWarps = kRasterThreads / 32;
+constexpr int kOvfKeep = 480;               // fragments composited per overflow pass
+constexpr int kOvfBuf = 1024;               // per-warp overflow buffer (power of two)
+constexpr int kOvfThreads = 128;
+
+struct TriSm {
+  int e[3];        // biased edge value (E + owned - 1) at the half-block's first pixel centre
+  int sx[3];       // change per pixel step in x
+  int sy[3];       // change per pixel step in y
+  float q0, d1, d2, inv;   // 1/w at v0, (q1 - q0), (q2 - q0), 1 / (float)area
+  uint32_t id;     // 2 * quad (view-local) + triangle
+  uint32_t flags;  // kTri* | (1 - owned_e) << (3 + e)
+  int X[3], Y[3];  // vertices after the orientation fix (64-bit path)
+};
+
+// dynamic shared memory of k_raster: per warp 64 triangle records, a 64-entry candidate
+// queue and, when fragments carry colours, 3 premultiplied vertex colours per triangle
+__host__ __device__ constexpr size_t raster_smem_bytes(bool vtx) {
+  return (size_t)kRasterWarps * 64 * (sizeof(TriSm) + sizeof(uint32_t)) +
+         (vtx ? (size_t)kRasterWarps * 64 * 3 * sizeof(float4) : 0);
+}
+
+// exact 64-bit edge values (unbiased) of a triangle at pixel (px, py)
+__device__ __forceinline__ void edges64(const TriSm& T, int px, int py, long long e[3]) {
+  const long long Px = 256LL * px + 128, Py = 256LL * py + 128;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int u = k == 0 ? 1 : (k == 1 ? 2 : 0);
+    const int w = k == 0 ? 2 : (k == 1 ? 0 : 1);
+    e[k] = (long long)(T.X[w] - T.X[u]) * (Py - T.Y[u]) - (long long)(T.Y[w] - T.Y[u]) * (Px - T.X[u]);
+  }
+}
+
+// Builds the per-half-block record of triangle t of a quad; returns false if the triangle
+// has zero area or its pixel AABB misses the half-block.
+__device__ __forceinline__ bool setup_tri(TriSm& T, const int X[4], const int Y[4], const float qv[4],
+                                          uint32_t info, int t, uint32_t jl, int ox, int oy,
+                                          int cor[3]) {
+  if (!(info & (t ? kInfoTri1 : kInfoTri0))) return false;
+  int ia = 0, ib = t ? 2 : 1, ic = t ? 3 : 2;
+  long long A = area2(X[ia], Y[ia], X[ib], Y[ib], X[ic], Y[ic]);
+  if (A < 0) { const int tmp = ib; ib = ic; ic = tmp; A = -A; }
+  const int xmin = min(X[ia], min(X[ib], X[ic])), xmax = max(X[ia], max(X[ib], X[ic]));
+  const int ymin = min(Y[ia], min(Y[ib], Y[ic])), ymax = max(Y[ia], max(Y[ib], Y[ic]));
+  if (ceil_div256((long long)xmin - 128) > ox + kHbW - 1 || floor_div256((long long)xmax - 128) < ox ||
+      ceil_div256((long long)ymin - 128) > oy + kHbH - 1 || floor_div256((long long)ymax - 128) < oy)
+    return false;
+  cor[0] = ia; cor[1] = ib; cor[2] = ic;
+  T.X[0] = X[ia]; T.X[1] = X[ib]; T.X[2] = X[ic];
+  T.Y[0] = Y[ia]; T.Y[1] = Y[ib]; T.Y[2] = Y[ic];
+  T.q0 = qv[ia];
+  T.d1 = __fsub_rn(qv[ib], qv[ia]);
+  T.d2 = __fsub_rn(qv[ic], qv[ia]);
+  T.inv = __fdiv_rn(1.0f, __ll2float_rn(A));
+  T.id = 2u * jl + (uint32_t)t;
+  uint32_t flags = kTriValid;
+  bool fast = true;
+  const long long P0x = 256LL * ox + 128, P0y = 256LL * oy + 128;
+  const long long lim = 1LL << 30;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int u = k == 0 ? 1 : (k == 1 ? 2 : 0);
+    const int w = k == 0 ? 2 : (k == 1 ? 0 : 1);
+    const long long dx = (long long)T.X[w] - T.X[u], dy = (long long)T.Y[w] - T.Y[u];
+    const bool owned = dy < 0 || (dy == 0 && dx > 0);
+    const long long e0 = dx * (P0y - T.Y[u]) - dy * (P0x - T.X[u]) + (owned ? 0 : -1);
+    const long long sx = -256 * dy, sy = 256 * dx;
+    const long long c1 = e0 + (kHbW - 1) * sx, c2 = e0 + (kHbH - 1) * sy, c3 = c1 + (kHbH - 1) * sy;
+    fast &= (e0 > -lim && e0 < lim && c1 > -lim && c1 < lim && c2 > -lim && c2 < lim && c3 > -lim && c3 < lim);
+    T.e[k] = (int)e0;
+    T.sx[k] = (int)sx;
+    T.sy[k] = (int)sy;
+    if (!owned) flags |= 1u << (3 + k);
+  }
+  if (fast) flags |= kTriFast;
+  T.flags = flags;
+  return true;
+}
+
+// Backward of the front-to-back composite for one pixel (flat per-quad RGBA). With
+// C = sum_i T_i a_i c_i, T_i = prod_{k<i} (1 - a_k), A = 1 - prod (1 - a_k):
+//   dC/dc_i = T_i a_i,   dC/da_i = T_i c_i - S_i / (1 - a_i),   dA/da_i = T_final / (1 - a_i)
+// where S_i = C_final - (C accumulated through fragment i) is the colour contributed by the
+// fragments behind i. C_final, T_final come from the forward image; the running sums are
+// recomputed with the forward's operations in the forward's order.
+struct GradPixel {
+  float gr, gg, gb, ga;      // dL/d(R, G, B, A) of the pixel
+  float fr, fg, fb, fT;      // forward colour and transmittance
+  float* grad;               // f32[Q][4] of the view
+};
+
+template <int K, bool VTX, bool BWD = false>
+struct PixelState {
+  unsigned long long s[K];
+  float4 c[VTX ? K : 1];
+  unsigned long long last;
+  float r, g, b, T;
+  bool flagged;
+  GradPixel gp;
+
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int i = 0; i < K; ++i) s[i] = kSent;
+    last = kSent;
+    r = g = b = 0.f;
+    T = 1.f;
+    flagged = false;
+  }
+
+  __device__ __forceinline__ void blend(unsigned long long key, float4 col, const ViewDev& V) {
+    const uint32_t j = (uint32_t)key >> 1;
+    if (!VTX) col = __ldg(reinterpret_cast<const float4*>(V.col) + j);
+    const float w = T * col.w;
+    r += w * col.x;
+    g += w * col.y;
+    b += w * col.z;
+    if (BWD) {
+      const float om = 1.0f - col.w;
+      float da = gp.gr * T * col.x + gp.gg * T * col.y + gp.gb * T * col.z;
+      if (om > 1e-6f) {
+        const float inv = 1.0f / om;
+        da -= (gp.gr * (gp.fr - r) + gp.gg * (gp.fg - g) + gp.gb * (gp.fb - b)) * inv;
+        da += gp.ga * gp.fT * inv;
+      }
+      float* gq = gp.grad + 4ull * j;
+      atomicAdd(gq + 0, gp.gr * w);
+      atomicAdd(gq + 1, gp.gg * w);
+      atomicAdd(gq + 2, gp.gb * w);
+      atomicAdd(gq + 3, da);
+    }
+    T *= 1.0f - col.w;
+  }
+
+  __device__ __forceinline__ void insert(unsigned long long x, float4 xc, const ViewDev& V) {
+    if (x > last) {   // nearer than a fragment already blended: order not guaranteed
+      flagged = true;
+      return;
+    }
+    const bool xfirst = x > s[0];
+    const unsigned long long ev = xfirst ? x : s[0];
+    const unsigned long long y = xfirst ? s[0] : x;
+    float4 evc = xc, yc = xc;
+    if (VTX) {
+      evc = xfirst ? xc : c[0];
+      yc = xfirst ? c[0] : xc;
+    }
+    // new slots = {s[1..K-1], y} in decreasing order
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const bool take_next = (i + 1 < K) && (s[i + 1 < K ? i + 1 : i] > y);
+      const bool take_y = (i == 0) || (s[i] > y);
+      const unsigned long long nxt = s[i + 1 < K ? i + 1 : i];
+      s[i] = take_next ? nxt : (take_y ? y : s[i]);
+      if (VTX) {
+        const float4 nc = c[i + 1 < K ? i + 1 : i];
+        c[i] = take_next ? nc : (take_y ? yc : c[i]);
+      }
+    }
+    if (ev != kSent) {
+      blend(ev, evc, V);
+      last = ev;
+    }
+  }
+
+  __device__ __forceinline__ void flush(const ViewDev& V) {
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (s[i] != kSent) blend(s[i], VTX ? c[i] : make_float4(0.f, 0.f, 0.f, 0.f), V);
+  }
+};
+
+__device__ __forceinline__ void write_pixel(const ViewDev& V, long long pidx, float r, float g, float b,
+                                            float T) {
+  const float a = 1.0f - T;
+  reinterpret_cast<float4*>(V.out)[pidx] = make_float4(r, g, b, a);
+  if (V.out8) {
+    const uint32_t c0 = __float2uint_rn(__fmul_rn(__saturatef(r), 255.0f));
+    const uint32_t c1 = __float2uint_rn(__fmul_rn(__saturatef(g), 255.0f));
+    const uint32_t c2 = __float2uint_rn(__fmul_rn(__saturatef(b), 255.0f));
+    const uint32_t c3 = __float2uint_rn(__fmul_rn(__saturatef(a), 255.0f));
+    reinterpret_cast<uint32_t*>(V.out8)[pidx] = c0 | (c1 << 8) | (c2 << 16) | (c3 << 24);
+  }
+}
+
+template <int K, bool VTX, bool BWD>
+__global__ __launch_bounds__(kRasterThreads) void k_raster(Ws ws) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lx = lane & (kHbW - 1), ly = lane >> 3;
+  TriSm* tris = reinterpret_cast<TriSm*>(smem) + warp * 64;
+  uint32_t* cand = reinterpret_cast<uint32_t*>(smem + (size_t)kRasterWarps * 64 * sizeof(TriSm)) + warp * 64;
+  float4* qcs = reinterpret_cast<float4*>(smem + (size_t)kRasterWarps * 64 * (sizeof(TriSm) + 4)) +
+                (size_t)warp * 64 * 3;
+  if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
+  const unsigned long long nitems = ws.ctrl->raster_items;
+  unsigned long long frag_total = 0;
+
+  for (;;) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(&ws.ctrl->raster_head, 1ull);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= nitems) break;
+    const int bin_g = (int)ws.bin_order[item / kHbPerBin];
+    const int hb = (int)(item % kHbPerBin);
+    const int v = view_of_bin(ws.views, ws.n_views, bin_g);
+    const ViewDev& V = ws.views[v];
+    const int b = bin_g - V.bin_base;
+    const int bx = b % V.nbx, by = b / V.nbx;
+    const int ox = (bx << kBinLog2) + (hb & 3) * kHbW, oy = (by << kBinLog2) + (hb >> 2) * kHbH;
+    if (ox >= V.width || oy >= V.height) continue;
+    const int px = ox + lx, py = oy + ly;
+    const bool pix_ok = px < V.width && py < V.height;
+    const uint32_t off = ws.bin_off[bin_g];
+    const int n = (int)(ws.bin_off[bin_g + 1] - off);
+    const bool vtx_view = V.color_mode == LR_COLOR_VERTEX;
+
+    PixelState<K, VTX, BWD> st;
+    st.init();
+    if (BWD && pix_ok) {
+      const long long pidx = (long long)py * V.width + px;
+      const float4 gq = reinterpret_cast<const float4*>(ws.grad_out)[pidx];
+      const float4 fq = reinterpret_cast<const float4*>(ws.fwd)[pidx];
+      st.gp.gr = gq.x; st.gp.gg = gq.y; st.gp.gb = gq.z; st.gp.ga = gq.w;
+      st.gp.fr = fq.x; st.gp.fg = fq.y; st.gp.fb = fq.z; st.gp.fT = 1.0f - fq.w;
+      st.gp.grad = ws.grad_col;
+    }
+    uint32_t cnt = 0;
+    unsigned long long hsh = 0;
+
+    auto process = [&](int nc) {
+      // ---- 2. triangle setup, one quad per lane ------------------------------------
+      if (lane < nc) {
+        const uint32_t rec = cand[lane];
+        const int4 A = ws.rec_xy[2ull * rec], B = ws.rec_xy[2ull * rec + 1];
+        const float4 Qv = ws.rec_q[rec];
+        const uint32_t info = ws.rec_info[rec];
+        const int X[4] = {A.x, A.z, B.x, B.z}, Y[4] = {A.y, A.w, B.y, B.w};
+        const float qv[4] = {Qv.x, Qv.y, Qv.z, Qv.w};
+        const uint32_t jl = (uint32_t)(rec - V.quad_base);
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          TriSm& T = tris[2 * lane + t];
+          int cor[3];
+          if (!setup_tri(T, X, Y, qv, info, t, jl, ox, oy, cor)) {
+            T.flags = 0;
+            continue;
+          }
+          if (VTX) {
+            float4* qc = qcs + (2 * lane + t) * 3;
+            if (!vtx_view) {
+              qc[0] = __ldg(reinterpret_cast<const float4*>(V.col) + jl);
+              T.flags |= kTriFlatCol;
+            } else {
+              uint4 vi;
+              if (V.idx) vi = __ldg(reinterpret_cast<const uint4*>(V.idx) + jl);
+              else vi = make_uint4(4 * jl, 4 * jl + 1, 4 * jl + 2, 4 * jl + 3);
+              const uint32_t vids[4] = {vi.x, vi.y, vi.z, vi.w};
+#pragma unroll
+              for (int k = 0; k < 3; ++k) {
+                const float4 cc = __ldg(reinterpret_cast<const float4*>(V.col) + vids[cor[k]]);
+                const float qk = qv[cor[k]];
+                qc[k] = make_float4(qk * cc.x, qk * cc.y, qk * cc.z, qk * cc.w);
+              }
+            }
+          }
+        }
+      }
+      __syncwarp();
+      // ---- 3. coverage: one bit per covering triangle --------------------------------
+      uint32_t m0 = 0, m1 = 0;
+      for (int c = 0; c < nc; ++c) {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const TriSm& T = tris[2 * c + t];
+          const uint32_t fl = T.flags;
+          if (!(fl & kTriValid)) continue;
+          bool cov;
+          if (fl & kTriFast) {
+            const int e0 = (int)((uint32_t)T.e[0] + (uint32_t)lx * (uint32_t)T.sx[0] + (uint32_t)ly * (uint32_t)T.sy[0]);
+            const int e1 = (int)((uint32_t)T.e[1] + (uint32_t)lx * (uint32_t)T.sx[1] + (uint32_t)ly * (uint32_t)T.sy[1]);
+            const int e2 = (int)((uint32_t)T.e[2] + (uint32_t)lx * (uint32_t)T.sx[2] + (uint32_t)ly * (uint32_t)T.sy[2]);
+            cov = (e0 | e1 | e2) >= 0;
+          } else {
+            long long e[3];
+            edges64(T, px, py, e);
+            cov = true;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              const bool owned = !(fl & (1u << (3 + k)));
+              cov &= e[k] > 0 || (e[k] == 0 && owned);
+            }
+          }
+          cov &= pix_ok;
+          if (t == 0) m0 |= (uint32_t)cov << c;
+          else m1 |= (uint32_t)cov << c;
+        }
+      }
+      // ---- 4. fragments in queue order through the K-slot sorter ---------------------
+      uint32_t bits = m0 | m1;
+      while (bits) {
+        const int c = __ffs(bits) - 1;
+        bits &= bits - 1;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          if (!(((t ? m1 : m0) >> c) & 1u)) continue;
+          const TriSm& T = tris[2 * c + t];
+          const uint32_t fl = T.flags;
+          float f1, f2;
+          if (fl & kTriFast) {
+            const int e1 = (int)((uint32_t)T.e[1] + (uint32_t)lx * (uint32_t)T.sx[1] + (uint32_t)ly * (uint32_t)T.sy[1] +
+                                 ((fl >> 4) & 1u));
+            const int e2 = (int)((uint32_t)T.e[2] + (uint32_t)lx * (uint32_t)T.sx[2] + (uint32_t)ly * (uint32_t)T.sy[2] +
+                                 ((fl >> 5) & 1u));
+            f1 = __int2float_rn(e1);
+            f2 = __int2float_rn(e2);
+          } else {
+            long long e[3];
+            edges64(T, px, py, e);
+            f1 = __ll2float_rn(e[1]);
+            f2 = __ll2float_rn(e[2]);
+          }
+          const float l1 = __fmul_rn(f1, T.inv);
+          const float l2 = __fmul_rn(f2, T.inv);
+          const float key = __fadd_rn(T.q0, __fadd_rn(__fmul_rn(l1, T.d1), __fmul_rn(l2, T.d2)));
+          const unsigned long long sk = ((unsigned long long)__float_as_uint(key) << 32) | T.id;
+          ++cnt;
+          if (V.hash) hsh += splitmix64(T.id);
+          if (st.flagged) continue;
+          float4 col = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (VTX) {
+            const float4* qc = qcs + (2 * c + t) * 3;
+            if (fl & kTriFlatCol) {
+              col = qc[0];
+            } else {
+              const float l0 = 1.0f - l1 - l2;
+              const float rk = __frcp_rn(key);
+              const float4 a0 = qc[0], a1 = qc[1], a2 = qc[2];
+              col.x = (l0 * a0.x + l1 * a1.x + l2 * a2.x) * rk;
+              col.y = (l0 * a0.y + l1 * a1.y + l2 * a2.y) * rk;
+              col.z = (l0 * a0.z + l1 * a1.z + l2 * a2.z) * rk;
+              col.w = (l0 * a0.w + l1 * a1.w + l2 * a2.w) * rk;
+            }
+          }
+          st.insert(sk, col, V);
+        }
+      }
+      __syncwarp();
+    };
+
+    // ---- 1. filter the bin's sorted references by the half-block rectangle -----------
+    int qn = 0;
+    for (int base = 0; base < n; base += 32) {
+      const int i = base + lane;
+      bool hit = false;
+      uint32_t rec = 0;
+      if (i < n) {
+        rec = ~(uint32_t)ws.refs[off + i];
+        if (rec < (uint64_t)ws.total_quads) {
+          const uint2 r = ws.rec_rect[rec];
+          hit = (int)(r.x & 0xffff) <= ox + kHbW - 1 && (int)(r.x >> 16) >= ox &&
+                (int)(r.y & 0xffff) <= oy + kHbH - 1 && (int)(r.y >> 16) >= oy;
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, hit);
+      if (hit) cand[qn + __popc(m & ((1u << lane) - 1u))] = rec;
+      qn += __popc(m);
+      __syncwarp();
+      if (qn >= 32) {
+        process(32);
+        const uint32_t keep = lane < qn - 32 ? cand[32 + lane] : 0u;
+        __syncwarp();
+        if (lane < qn - 32) cand[lane] = keep;
+        __syncwarp();
+        qn -= 32;
+      }
+    }
+    if (qn > 0) process(qn);
+
+    // ---- finish the half-block ---------------------------------------------------------
+    if (!st.flagged) st.flush(V);
+    if (pix_ok) {
+      const long long pidx = (long long)py * V.width + px;
+      if (!BWD && V.cnt) V.cnt[pidx] = cnt;
+      if (!BWD && V.hash) V.hash[pidx] = hsh;
+      if (!st.flagged) {
+        if (!BWD) write_pixel(V, pidx, st.r, st.g, st.b, st.T);
+      } else {
+        const unsigned long long slot = atomicAdd(&ws.ctrl->ovf_count, 1ull);
+        ws.ovf_list[slot] = (uint32_t)(V.pix_base + pidx);
+      }
+    }
+    frag_total += cnt;
+  }
+  // fragments of all pixels this warp rendered
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) frag_total += __shfl_xor_sync(0xffffffffu, frag_total, o);
+  if (lane == 0 && frag_total) atomicAdd(&ws.ctrl->fragments, frag_total);
+}
+
+}  // namespace lr
+
+// Each translation unit lr_raster_k<K>.cu instantiates the rasteriser for one sorter
+// capacity K (both colour layouts) through this macro, so the variants compile in
+// parallel.
+#define LR_DEFINE_RASTER(KK)                                                                  \
+  namespace lr {                                                                              \
+  cudaError_t prepare_raster_##KK(int* blocks_flat, int* blocks_vtx, int* blocks_bwd) {       \
+    cudaError_t e = cudaFuncSetAttribute(k_raster<KK, false, false>,                          \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+                                         (int)raster_smem_bytes(false));                      \
+    if (e != cudaSuccess) return e;                                                           \
+    e = cudaFuncSetAttribute(k_raster<KK, true, false>,                                       \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,                     \
+                             (int)raster_smem_bytes(true));                                   \
+    if (e != cudaSuccess) return e;                                                           \
+    e = cudaFuncSetAttribute(k_raster<KK, false, true>,                                       \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,                     \
+                             (int)raster_smem_bytes(false));                                  \
+    if (e != cudaSuccess) return e;                                                           \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_flat, k_raster<KK, false, false>, \
+                                                      kRasterThreads, raster_smem_bytes(false)); \
+    if (e != cudaSuccess) return e;                                                           \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_bwd, k_raster<KK, false, true>,  \
+                                                      kRasterThreads, raster_smem_bytes(false)); \
+    if (e != cudaSuccess) return e;                                                           \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_vtx, k_raster<KK, true, false>, \
+                                                         kRasterThreads, raster_smem_bytes(true)); \
+  }                                                                                           \
+  cudaError_t launch_raster_##KK(int mode, const Ws& ws, int grid, cudaStream_t st) {         \
+    if (mode == 1)                                                                            \
+      k_raster<KK, true, false><<<grid, kRasterThreads, raster_smem_bytes(true), st>>>(ws);   \
+    else if (mode == 2)                                                                       \
+      k_raster<KK, false, true><<<grid, kRasterThreads, raster_smem_bytes(false), st>>>(ws);  \
+    else                                                                                      \
+      k_raster<KK, false, false><<<grid, kRasterThreads, raster_smem_bytes(false), st>>>(ws); \
+    return cudaGetLastError();                                                                \
+  }                                                                                           \
+  }

@@ -1,0 +1,3 @@
+// Rasteriser instantiation for a per-pixel sorter of capacity K = 3.
+#include "lr_raster.cuh"
+LR_DEFINE_RASTER(3)

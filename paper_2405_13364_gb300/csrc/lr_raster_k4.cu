@@ -1,0 +1,3 @@
+// Rasteriser instantiation for a per-pixel sorter of capacity K = 4.
+#include "lr_raster.cuh"
+LR_DEFINE_RASTER(4)
