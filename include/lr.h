@@ -199,6 +199,51 @@ lr_status lr_get_stats(lr_ctx* ctx, lr_stats* stats);
 /* Human-readable description of the last error on this context (never NULL). */
 const char* lr_last_error(const lr_ctx* ctx);
 
+/* ---- serving: continuous batching of render requests ------------------------------
+ * (Not in the paper; it serves the single-frame pipeline.) A host thread keeps
+ * num_slots batches in flight, each on its own CUDA stream with its own device workspace
+ * of slot_workspace_bytes (allocated by lr_server_start, freed by lr_server_stop or
+ * lr_destroy). Queued requests are admitted in arrival order into the next free slot
+ * while the batch fits the slot's workspace and has at most max_batch_views views; each
+ * batch is one multi-view render (lr_render_batch). A request whose view does not fit a
+ * slot alone completes with LR_ERR_OOM. While a server runs on a context, call only
+ * lr_submit / lr_poll / lr_poll_info / lr_server_get_stats / lr_server_stop on it (these
+ * may be called from any thread). */
+typedef struct {
+  int32_t num_slots;             /* batches in flight at once; default 2 */
+  int32_t max_batch_views;       /* views per batch; default 16 */
+  int64_t slot_workspace_bytes;  /* device workspace per slot; default 512 MiB */
+  int32_t poll_interval_us;      /* completion polling period of the server thread; default 20 */
+  int32_t reserved;
+} lr_server_config;
+
+typedef struct {
+  uint64_t submit_ns, launch_ns, done_ns;   /* lr_now_ns() clock */
+  int32_t batch_views;                      /* views in the batch that rendered it */
+  int32_t reserved;
+} lr_request_info;
+
+typedef struct {
+  int64_t submitted, completed, failed, batches, batched_views, split_batches, queued;
+} lr_server_stats;
+
+lr_status lr_server_start(lr_ctx* ctx, const lr_server_config* config);
+/* Finishes every queued and running request, then stops the thread and frees the slots. */
+lr_status lr_server_stop(lr_ctx* ctx);
+/* Queue a render request. view (host struct) holds device pointers to the scene and the
+ * outputs, which the caller keeps alive and unmodified until lr_poll reports completion. */
+lr_status lr_submit(lr_ctx* ctx, const lr_view* view, uint64_t* ticket);
+/* Completion of a ticket, waiting at most timeout_us microseconds. Returns LR_OK with
+ * *result = the request's status once it has finished (the ticket is then released),
+ * LR_PENDING (timeout_us == 0) or LR_ERR_TIMEOUT (timeout_us > 0) if it has not. */
+lr_status lr_poll(lr_ctx* ctx, uint64_t ticket, int32_t timeout_us, lr_status* result);
+/* lr_poll plus the request's submit / launch / completion times and batch size. */
+lr_status lr_poll_info(lr_ctx* ctx, uint64_t ticket, int32_t timeout_us, lr_status* result,
+                       lr_request_info* info);
+lr_status lr_server_get_stats(lr_ctx* ctx, lr_server_stats* stats);
+/* The monotonic clock (nanoseconds) used for lr_request_info. */
+uint64_t lr_now_ns(void);
+
 #ifdef __cplusplus
 }
 #endif

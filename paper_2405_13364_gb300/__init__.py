@@ -19,7 +19,8 @@ from . import _binding as B
 from ._binding import (LR_COLOR_FLAT, LR_COLOR_VERTEX, LR_ERR_OVERFLOW, LR_FLAG_TIMING, LR_OK,
                        LrError, lr_camera, lr_config, lr_quads, lr_stats, lr_target, lr_view)
 
-__all__ = ["Renderer", "DeviceScene", "LrError", "LR_COLOR_FLAT", "LR_COLOR_VERTEX", "load_library"]
+__all__ = ["Renderer", "DeviceScene", "Server", "LrError", "LR_COLOR_FLAT", "LR_COLOR_VERTEX",
+           "composite", "load_library"]
 
 
 def load_library():
@@ -242,3 +243,56 @@ def composite(colors: torch.Tensor, renderer: Renderer, scene: DeviceScene, widt
     """Differentiable render w.r.t. flat per-quad RGBA colors f32[Q][4] (CUDA tensor).
     Coverage and depth order are exact and piecewise constant: they get no gradient."""
     return _Composite.apply(colors, renderer, scene, width, height)
+
+
+class Server:
+    """Continuous-batching render server (lr_server_start / lr_submit / lr_poll).
+
+    Owns its own context (created with the renderer options given here). Submitted
+    scenes and outputs are kept alive until their request completes.
+    """
+
+    def __init__(self, sorter_k: int = 3, num_slots: int = 2, max_batch_views: int = 16,
+                 slot_workspace_bytes: int = 512 << 20, poll_interval_us: int = 20,
+                 max_width: int = 2560, max_height: int = 2048, device=None):
+        self.renderer = Renderer(sorter_k=sorter_k, max_width=max_width, max_height=max_height,
+                                 device=device)
+        self.ctx = self.renderer.ctx
+        cfg = B.lr_server_config(num_slots, max_batch_views, slot_workspace_bytes, poll_interval_us, 0)
+        B.lr_server_start(self.ctx, cfg)
+        self._live = {}
+        self.running = True
+
+    def submit(self, scene: DeviceScene, width: int, height: int, out: Outputs | None = None,
+               **outputs) -> int:
+        out = out if out is not None else self.renderer.make_outputs(width, height, **outputs)
+        view = Renderer.view_struct(scene, width, height, out)
+        t = B.lr_submit(self.ctx, view)
+        self._live[t] = (scene, out)
+        return t
+
+    def poll(self, ticket: int, timeout_us: int = 0):
+        """None while pending; else (status, outputs, info dict with ns timestamps)."""
+        st, res, info = B.lr_poll_info(self.ctx, ticket, timeout_us)
+        if st != LR_OK:
+            return None
+        _, out = self._live.pop(ticket)
+        return res, out, dict(submit_ns=info.submit_ns, launch_ns=info.launch_ns,
+                              done_ns=info.done_ns, batch_views=info.batch_views)
+
+    def stats(self) -> dict:
+        st = B.lr_server_get_stats(self.ctx)
+        return {n: getattr(st, n) for n, _ in B.lr_server_stats._fields_}
+
+    @staticmethod
+    def now_ns() -> int:
+        return B.lr_now_ns()
+
+    def stop(self):
+        if self.running:
+            B.lr_server_stop(self.ctx)
+            self.running = False
+
+    def close(self):
+        self.stop()
+        self.renderer.close()

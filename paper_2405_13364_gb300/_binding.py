@@ -83,6 +83,23 @@ class lr_ws_layout(ctypes.Structure):
                 ("refs_capacity", ctypes.c_int64)]
 
 
+class lr_server_config(ctypes.Structure):
+    _fields_ = [("num_slots", ctypes.c_int32), ("max_batch_views", ctypes.c_int32),
+                ("slot_workspace_bytes", ctypes.c_int64), ("poll_interval_us", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class lr_request_info(ctypes.Structure):
+    _fields_ = [("submit_ns", ctypes.c_uint64), ("launch_ns", ctypes.c_uint64),
+                ("done_ns", ctypes.c_uint64), ("batch_views", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class lr_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "batches",
+                                             "batched_views", "split_batches", "queued")]
+
+
 # every entry point declared in include/lr.h, with its ctypes signature
 _P = ctypes.c_void_p
 _SIGNATURES = {
@@ -105,6 +122,14 @@ _SIGNATURES = {
                                            ctypes.c_size_t, ctypes.POINTER(lr_ws_layout)]),
     "lr_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(lr_stats)]),
     "lr_last_error": (ctypes.c_char_p, [_P]),
+    "lr_server_start": (ctypes.c_int, [_P, ctypes.POINTER(lr_server_config)]),
+    "lr_server_stop": (ctypes.c_int, [_P]),
+    "lr_submit": (ctypes.c_int, [_P, ctypes.POINTER(lr_view), ctypes.POINTER(ctypes.c_uint64)]),
+    "lr_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int)]),
+    "lr_poll_info": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(lr_request_info)]),
+    "lr_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(lr_server_stats)]),
+    "lr_now_ns": (ctypes.c_uint64, []),
 }
 
 _lib = None
@@ -214,3 +239,41 @@ def lr_get_stats(ctx, raise_on_error: bool = True) -> lr_stats:
 
 def lr_last_error(ctx) -> str:
     return (load().lr_last_error(ctx) or b"").decode(errors="replace")
+
+
+def lr_server_start(ctx, config: lr_server_config):
+    _check(ctx, load().lr_server_start(ctx, ctypes.byref(config)), "lr_server_start")
+
+
+def lr_server_stop(ctx):
+    _check(ctx, load().lr_server_stop(ctx), "lr_server_stop")
+
+
+def lr_submit(ctx, view: lr_view) -> int:
+    t = ctypes.c_uint64()
+    _check(ctx, load().lr_submit(ctx, ctypes.byref(view), ctypes.byref(t)), "lr_submit")
+    return t.value
+
+
+def lr_poll(ctx, ticket: int, timeout_us: int = 0):
+    """(call status, request status): call status LR_OK once the request has finished."""
+    res = ctypes.c_int(LR_PENDING)
+    st = load().lr_poll(ctx, ticket, timeout_us, ctypes.byref(res))
+    return st, res.value
+
+
+def lr_poll_info(ctx, ticket: int, timeout_us: int = 0):
+    res = ctypes.c_int(LR_PENDING)
+    info = lr_request_info()
+    st = load().lr_poll_info(ctx, ticket, timeout_us, ctypes.byref(res), ctypes.byref(info))
+    return st, res.value, info
+
+
+def lr_server_get_stats(ctx) -> lr_server_stats:
+    out = lr_server_stats()
+    _check(ctx, load().lr_server_get_stats(ctx, ctypes.byref(out)), "lr_server_get_stats")
+    return out
+
+
+def lr_now_ns() -> int:
+    return load().lr_now_ns()

@@ -22,6 +22,7 @@
 
 #include "lr_common.cuh"
 #include "lr_raster.cuh"
+#include "lr_serve.h"
 
 namespace lr {
 __global__ void k_init(Ws ws, unsigned long long refs_cap);
@@ -178,8 +179,12 @@ struct lr_ctx {
   bool last_timed = false;
   cudaEvent_t ev[9] = {};
   Ctrl* host_ctrl = nullptr;   // pinned
+  lr_server* server = nullptr;
   char err[512] = {0};
 };
+
+lr_server** lr_internal_server_slot(lr_ctx* ctx) { return &ctx->server; }
+const lr_config* lr_internal_config(const lr_ctx* ctx) { return &ctx->cfg; }
 
 static lr_status fail(lr_ctx* c, lr_status s, const char* fmt, const char* detail = "") {
   if (c) snprintf(c->err, sizeof(c->err), fmt, detail);
@@ -246,6 +251,7 @@ extern "C" lr_status lr_create(const lr_config* config, lr_ctx** out_ctx) {
 
 extern "C" lr_status lr_destroy(lr_ctx* ctx) {
   if (!ctx) return LR_ERR_INVALID_ARG;
+  if (ctx->server) lr_server_stop(ctx);
   for (int i = 0; i < 9; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   if (ctx->host_ctrl) cudaFreeHost(ctx->host_ctrl);

@@ -149,7 +149,7 @@ struct PixelState {
     r += w * col.x;
     g += w * col.y;
     b += w * col.z;
-    if (BWD) {
+    if (BWD && gp.grad) {
       const float om = 1.0f - col.w;
       float da = gp.gr * T * col.x + gp.gg * T * col.y + gp.gb * T * col.z;
       if (om > 1e-6f) {
@@ -251,13 +251,13 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster(Ws ws) {
 
     PixelState<K, VTX, BWD> st;
     st.init();
+    st.gp.grad = nullptr;
     if (BWD && pix_ok) {
       const long long pidx = (long long)py * V.width + px;
       const float4 gq = reinterpret_cast<const float4*>(ws.grad_out)[pidx];
       const float4 fq = reinterpret_cast<const float4*>(ws.fwd)[pidx];
       st.gp.gr = gq.x; st.gp.gg = gq.y; st.gp.gb = gq.z; st.gp.ga = gq.w;
       st.gp.fr = fq.x; st.gp.fg = fq.y; st.gp.fb = fq.z; st.gp.fT = 1.0f - fq.w;
-      st.gp.grad = ws.grad_col;
     }
     uint32_t cnt = 0;
     unsigned long long hsh = 0;
@@ -382,6 +382,18 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster(Ws ws) {
       __syncwarp();
     };
 
+    // The backward pass streams the half-block twice: first without gradients, to learn
+    // which pixels the sorter cannot order (those are left to the exact path, which
+    // emits their whole gradient), then with gradients for the other pixels only.
+    bool pre_flagged = false;
+    for (int pass = BWD ? 0 : 1; pass < 2; ++pass) {
+    if (BWD) {
+      st.init();
+      st.flagged = pre_flagged;
+      st.gp.grad = (pass == 1 && pix_ok) ? ws.grad_col : nullptr;
+      cnt = 0;
+      hsh = 0;
+    }
     // ---- 1. filter the bin's sorted references by the half-block rectangle -----------
     int qn = 0;
     for (int base = 0; base < n; base += 32) {
@@ -410,6 +422,8 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster(Ws ws) {
       }
     }
     if (qn > 0) process(qn);
+    if (pass == 0) pre_flagged = st.flagged;
+    }
 
     // ---- finish the half-block ---------------------------------------------------------
     if (!st.flagged) st.flush(V);

@@ -1,0 +1,12 @@
+// lr_serve.h -- internal link between the context (lr_api.cu) and the serving loop
+// (lr_serve.cu).
+#pragma once
+
+#include "lr.h"
+
+struct lr_server;
+
+// the context's server pointer (nullptr when no server runs)
+lr_server** lr_internal_server_slot(lr_ctx* ctx);
+// the configuration the context was created with (defaults filled in)
+const lr_config* lr_internal_config(const lr_ctx* ctx);
