@@ -295,6 +295,30 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_profile(args):
+    """A short, self-contained run for ncu: a few frames of the benchmark workload, no
+    timing, no CPU baseline. Kernel launch order per frame: k_write_views, k_init, k_setup,
+    k_bin_count, k_bin_scan, k_bin_scatter, k_bin_sort, k_raster, k_overflow."""
+    import torch
+
+    import paper_2405_13364_gb300 as P
+    import scenegen
+    torch.cuda.set_device(0)
+    scene = {"layers": scenegen.config_layers_1080p, "particles": scenegen.config_particles_1080p,
+             "frustum": scenegen.config_small_frustum, "diff": scenegen.config_diff_1024}[args.workload]()
+    r = P.Renderer(sorter_k=args.k)
+    ds = P.DeviceScene.from_scene(scene)
+    out = r.make_outputs(scene.width, scene.height)
+    view = r.view_struct(ds, scene.width, scene.height, out)
+    r.render_views([view])
+    for _ in range(args.steps):
+        r.render_views([view], check=False)
+    torch.cuda.synchronize()
+    st = r.stats()
+    print(json.dumps({"profile_workload": args.workload, "frames": args.steps + 1,
+                      "fragments": st["fragments"], "overflow_pixels": st["overflow_pixels"]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -303,8 +327,12 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="short run for ncu (see run_profile)")
+    ap.add_argument("--workload", default="layers", choices=["layers", "particles", "frustum", "diff"])
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
