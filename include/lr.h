@@ -199,6 +199,38 @@ lr_status lr_get_stats(lr_ctx* ctx, lr_stats* stats);
 /* Human-readable description of the last error on this context (never NULL). */
 const char* lr_last_error(const lr_ctx* ctx);
 
+/* ---- rendering without any allocation -------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory when they render: for example a plugin that a host application
+ * calls once per frame, where the host owns all device memory through its own pool and
+ * forbids cudaMalloc after start-up (an allocation there can stall every stream of the
+ * process and may not fit the host's memory budget), so such a caller also cannot provide
+ * the workspace lr_render needs.
+ *
+ * lr_render_noalloc renders one frame like lr_render with the default sorter capacity
+ * (K = 3), but uses as its workspace a device array of LR_NOALLOC_SCRATCH_BYTES bytes that
+ * is part of the library's device code (every GPU on which that code is loaded holds it
+ * until the process exits). It needs no lr_ctx and calls no allocating function (no
+ * cudaMalloc / cudaFree / cudaMallocHost, no host heap).
+ *  - quads, camera: as for lr_render (device scene, host camera struct).
+ *  - out_rgba: device f32[H][W][4], 16-byte aligned; written when the stream reaches it.
+ *  - device_status: NULL, or a device int32 that receives the GPU-side status of this call
+ *    (LR_OK, LR_ERR_OVERFLOW if the scene's bin references did not fit the array,
+ *    LR_ERR_INVALID_ARG for out-of-range vertex indices); read it after the stream syncs.
+ *  - Returns LR_ERR_TOO_LARGE, before any GPU work, when the scene's records plus at least
+ *    two bin references per quad do not fit in LR_NOALLOC_SCRATCH_BYTES (roughly: up to
+ *    about 500k quads at 1920x1080, or 1M quads at 256x256); LR_ERR_INVALID_ARG for bad
+ *    arguments; LR_ERR_CUDA if a launch or the set-up failed.
+ *  - The first call on each device (with that device current) looks up the array's
+ *    address and sets kernel attributes; make that first call before any stream capture.
+ *  - All calls share the array, which keeps the last call's contents; each call zeroes
+ *    what must start at zero. Calls whose GPU work overlaps (e.g. on two streams) race on
+ *    the array: serialise them. */
+#define LR_NOALLOC_SCRATCH_BYTES (64ull << 20)
+lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* camera, int32_t width,
+                            int32_t height, float* out_rgba, int32_t* device_status,
+                            lr_stream stream);
+
 /* ---- serving: continuous batching of render requests ------------------------------
  * (Not in the paper; it serves the single-frame pipeline.) A host thread keeps
  * num_slots batches in flight, each on its own CUDA stream with its own device workspace

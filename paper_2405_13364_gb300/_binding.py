@@ -130,6 +130,8 @@ _SIGNATURES = {
                                     ctypes.POINTER(lr_request_info)]),
     "lr_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(lr_server_stats)]),
     "lr_now_ns": (ctypes.c_uint64, []),
+    "lr_render_noalloc": (ctypes.c_int, [ctypes.POINTER(lr_quads), ctypes.POINTER(lr_camera),
+                                         ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
 }
 
 _lib = None
@@ -277,3 +279,10 @@ def lr_server_get_stats(ctx) -> lr_server_stats:
 
 def lr_now_ns() -> int:
     return load().lr_now_ns()
+
+
+def lr_render_noalloc(quads: lr_quads, camera: lr_camera, width: int, height: int, out_rgba: int,
+                      device_status: int, stream: int) -> int:
+    """Returns the call's lr_status (no exception: callers test the documented codes)."""
+    return load().lr_render_noalloc(ctypes.byref(quads), ctypes.byref(camera), width, height,
+                                    out_rgba, device_status, stream)
