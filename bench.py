@@ -38,6 +38,29 @@ SM_COUNT = 152
 LANES_PER_SM_CLK = 128
 
 
+def _workloads():
+    import scenegen
+    return {
+        "layers": ("layers-1080p: 1920x1080, 32 wavy layers x 256x128 = 1,048,576 indexed quads, "
+                   "per-vertex RGBA, mean depth complexity 24", lambda s: scenegen.config_layers_1080p(seed=s)),
+        "particles": ("particles-1080p: 1920x1080, 2,000,000 camera-facing quads 2-16 px, flat RGBA, "
+                      "centre depth complexity > 500", lambda s: scenegen.config_particles_1080p(seed=s)),
+        "frustum": ("frustum-256: 256x256, 2,000 random parallelograms, flat RGBA",
+                    lambda s: scenegen.config_small_frustum(seed=s)),
+        "diff": ("layers-1024: 1024x1024, 32 layers x 128x128 = 524,288 quads, flat RGBA",
+                 lambda s: scenegen.config_diff_1024(seed=s)),
+    }
+
+
+class _LazyWorkloads(dict):
+    def __missing__(self, key):
+        self.update(_workloads())
+        return dict.__getitem__(self, key)
+
+
+WORKLOADS = _LazyWorkloads()
+
+
 def _env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -147,7 +170,7 @@ def run_gpu(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     dev = torch.device("cuda", local)
 
-    scene = scenegen.config_layers_1080p(seed=rank)
+    scene = WORKLOADS[args.workload][1](rank)
     W, H = scene.width, scene.height
     r = P.Renderer(sorter_k=args.k, timing=True)
     ds = P.DeviceScene.from_scene(scene, device=dev)
@@ -193,20 +216,21 @@ def run_gpu(args):
 
     # ---- end to end through the public API with host buffers -----------------------------
     host_pos = torch.from_numpy(scene.positions).pin_memory()
-    host_idx = torch.from_numpy(scene.indices.view(np.int32)).pin_memory()
+    host_idx = None if scene.indices is None else torch.from_numpy(scene.indices.view(np.int32)).pin_memory()
     host_col = torch.from_numpy(scene.colors).pin_memory()
     host_out = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
-    dpos, didx, dcol = torch.empty_like(host_pos, device=dev), torch.empty_like(host_idx, device=dev), \
-        torch.empty_like(host_col, device=dev)
+    dpos, dcol = torch.empty_like(host_pos, device=dev), torch.empty_like(host_col, device=dev)
+    didx = None if host_idx is None else torch.empty_like(host_idx, device=dev)
     e_scene = P.DeviceScene(dpos, didx, dcol, scene.color_mode, ds.view_proj, ds.near, ds.far)
     e_out = r.make_outputs(W, H)
     e_view = r.view_struct(e_scene, W, H, e_out)
-    h2d = host_pos.numel() * 4 + host_idx.numel() * 4 + host_col.numel() * 4
+    h2d = host_pos.numel() * 4 + (0 if host_idx is None else host_idx.numel() * 4) + host_col.numel() * 4
     d2h = host_out.numel() * 4
 
     def e2e_step():
         dpos.copy_(host_pos, non_blocking=True)
-        didx.copy_(host_idx, non_blocking=True)
+        if didx is not None:
+            didx.copy_(host_idx, non_blocking=True)
         dcol.copy_(host_col, non_blocking=True)
         r.render_views([e_view], check=False)
         host_out.copy_(e_out["rgba"], non_blocking=True)
@@ -259,11 +283,12 @@ def run_gpu(args):
                "sample": f"{n_frames} full 1920x1080 frames ({dt:.1f} s)"}
 
     line = {
-        "metric": METRIC, "value": round(value, 3), "unit": "Gfrag/s", "n_gpus": world,
+        "metric": METRIC if args.workload == "layers" else f"Gfrag/s ({args.workload})",
+        "value": round(value, 3), "unit": "Gfrag/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "frame": "1920x1080", "quads": scene.num_quads,
+        "config": {"workload": WORKLOADS[args.workload][0], "frame": f"{W}x{H}", "quads": scene.num_quads,
                    "fragments_per_frame": frags, "sorter_k": args.k,
                    "l2": "flushed before every step (512 MiB write, outside the timed events)",
                    "parallelism": f"replicas x{world} (one frame per GPU per step)"},

@@ -177,6 +177,20 @@ lr_status lr_render(lr_ctx* ctx, const lr_quads* quads, const lr_camera* camera,
 lr_status lr_render_batch(lr_ctx* ctx, int32_t n_views, const lr_view* views, void* workspace,
                           size_t workspace_bytes, lr_stream stream);
 
+/* ---- captured batches -------------------------------------------------------------
+ * lr_graph_create captures the launch sequence of lr_render_batch for these views into a
+ * CUDA graph bound to this workspace. lr_graph_launch replays it on a stream; views may
+ * be NULL (render the captured views again) or new views with the same shapes (per view:
+ * width, height, num_quads, color_mode); scene and output pointers and cameras may change.
+ * Replays read the view descriptors from one of two pinned host buffers owned by the
+ * graph; a launch waits (host side) for the replay two launches back. The graph, its
+ * workspace and the context must outlive every replay; lr_get_stats reports the last one. */
+typedef struct lr_graph lr_graph;
+lr_status lr_graph_create(lr_ctx* ctx, int32_t n_views, const lr_view* views, void* workspace,
+                          size_t workspace_bytes, lr_graph** out_graph);
+lr_status lr_graph_launch(lr_graph* graph, const lr_view* views, lr_stream stream);
+lr_status lr_graph_destroy(lr_graph* graph);
+
 /* Backward pass of the compositing with respect to flat per-quad RGBA.
  * grad_out: device f32[H][W][4] = dL/d(R, G, B, A) of the rendered image.
  * fwd_rgba: device f32[H][W][4] = the forward image of the same scene (as lr_render wrote
@@ -263,7 +277,9 @@ lr_status lr_server_start(lr_ctx* ctx, const lr_server_config* config);
 /* Finishes every queued and running request, then stops the thread and frees the slots. */
 lr_status lr_server_stop(lr_ctx* ctx);
 /* Queue a render request. view (host struct) holds device pointers to the scene and the
- * outputs, which the caller keeps alive and unmodified until lr_poll reports completion. */
+ * outputs, which the caller keeps alive and unmodified until lr_poll reports completion.
+ * Arguments are checked as lr_render_batch checks them; a bad request is refused here
+ * (LR_ERR_INVALID_ARG / LR_ERR_TOO_LARGE) and never joins a batch. */
 lr_status lr_submit(lr_ctx* ctx, const lr_view* view, uint64_t* ticket);
 /* Completion of a ticket, waiting at most timeout_us microseconds. Returns LR_OK with
  * *result = the request's status once it has finished (the ticket is then released),

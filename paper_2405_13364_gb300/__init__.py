@@ -182,6 +182,11 @@ class Renderer:
         self.render_views(views, stream, check)
         return outs
 
+    def capture(self, items, stream=None, **outputs) -> "GraphBatch":
+        """Capture a multi-view render of items [(DeviceScene, width, height)] into a CUDA
+        graph on a workspace of its own; replays may swap scenes/cameras of equal shape."""
+        return GraphBatch(self, items, stream, **outputs)
+
     def stats(self) -> dict:
         st = B.lr_get_stats(self.ctx, raise_on_error=False)
         names = ["setup", "count", "scan", "scatter", "sort", "raster", "overflow", "total"]
@@ -219,6 +224,46 @@ class Renderer:
                 raise LrError(st.status, B.lr_last_error(self.ctx))
             return grad
         raise LrError(LR_ERR_OVERFLOW, "bin references kept exceeding the workspace")
+
+
+class GraphBatch:
+    """A captured multi-view render (lr_graph_create / lr_graph_launch)."""
+
+    def __init__(self, renderer: Renderer, items, stream=None, **outputs):
+        self.r = renderer
+        self.items = list(items)
+        self.outs = [renderer.make_outputs(w, h, **outputs) for _, w, h in self.items]
+        self.views = [Renderer.view_struct(s, w, h, o) for (s, w, h), o in zip(self.items, self.outs)]
+        # size the workspace with one checked render (grows it on reference overflow)
+        renderer.render_views(self.views, stream)
+        need = renderer._ws_bytes
+        self._ws = torch.empty(need + 256, dtype=torch.uint8, device=renderer.device)
+        self._ptr = (int(self._ws.data_ptr()) + 255) & ~255
+        torch.cuda.synchronize(renderer.device)
+        self.graph = B.lr_graph_create(renderer.ctx, self.views, self._ptr, need)
+
+    def launch(self, items=None, stream=None):
+        """Replay; items (same shapes as captured) replaces scenes/cameras/outputs."""
+        stream = torch.cuda.current_stream(self.r.device) if stream is None else stream
+        views = None
+        if items is not None:
+            self.items = list(items)
+            views = [Renderer.view_struct(s, w, h, o) for (s, w, h), o in zip(self.items, self.outs)]
+            self.views = views
+        B.lr_graph_launch(self.r.ctx, self.graph, views, stream.cuda_stream)
+        return self.outs
+
+    def close(self):
+        if self.graph:
+            torch.cuda.synchronize(self.r.device)
+            B.lr_graph_destroy(self.graph)
+            self.graph = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class _Composite(torch.autograd.Function):

@@ -130,6 +130,10 @@ _SIGNATURES = {
                                     ctypes.POINTER(lr_request_info)]),
     "lr_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(lr_server_stats)]),
     "lr_now_ns": (ctypes.c_uint64, []),
+    "lr_graph_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(lr_view), _P, ctypes.c_size_t,
+                                       ctypes.POINTER(_P)]),
+    "lr_graph_launch": (ctypes.c_int, [_P, ctypes.POINTER(lr_view), _P]),
+    "lr_graph_destroy": (ctypes.c_int, [_P]),
     "lr_render_noalloc": (ctypes.c_int, [ctypes.POINTER(lr_quads), ctypes.POINTER(lr_camera),
                                          ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
 }
@@ -286,3 +290,20 @@ def lr_render_noalloc(quads: lr_quads, camera: lr_camera, width: int, height: in
     """Returns the call's lr_status (no exception: callers test the documented codes)."""
     return load().lr_render_noalloc(ctypes.byref(quads), ctypes.byref(camera), width, height,
                                     out_rgba, device_status, stream)
+
+
+def lr_graph_create(ctx, views, workspace: int, workspace_bytes: int):
+    arr = (lr_view * len(views))(*views)
+    out = _P()
+    _check(ctx, load().lr_graph_create(ctx, len(views), arr, workspace, workspace_bytes, ctypes.byref(out)),
+           "lr_graph_create")
+    return out
+
+
+def lr_graph_launch(ctx, graph, views, stream: int):
+    arr = None if views is None else (lr_view * len(views))(*views)
+    _check(ctx, load().lr_graph_launch(graph, arr, stream), "lr_graph_launch")
+
+
+def lr_graph_destroy(graph):
+    _check(None, load().lr_graph_destroy(graph), "lr_graph_destroy")

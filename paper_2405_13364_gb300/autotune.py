@@ -1,0 +1,103 @@
+"""Autotuner for the rasteriser's launch parameters.
+
+Tunable here: the per-pixel sorter capacity K (the paper's depth-filter size, Sec. 2
+"Sample blending"; every K gives the identical, exact image: a smaller K only sends more
+pixels down the exact overflow path) and the number of persistent rasteriser CTAs per SM.
+Bin size (32x32) and half-block shape (8x4) are fixed in this build.
+
+The tuner renders the workload with every candidate, checks that all candidates produce
+the same image bit for bit, times each with CUDA events (median of `reps`), and caches the
+winner in a JSON file keyed by (GPU name, resolution bucket, quad-count bucket, colour
+mode). The cache path is $LR_AUTOTUNE_CACHE, else ~/.cache/lucidraster_gb300/autotune.json.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import statistics
+
+import torch
+
+DEFAULT_KS = (1, 2, 3, 4, 6, 8)
+
+
+def cache_path() -> str:
+    p = os.environ.get("LR_AUTOTUNE_CACHE")
+    if p:
+        return p
+    return os.path.join(os.path.expanduser("~"), ".cache", "lucidraster_gb300", "autotune.json")
+
+
+def workload_key(width: int, height: int, num_quads: int, color_mode: int, device=None) -> str:
+    name = torch.cuda.get_device_name(device)
+    px = width * height
+    return f"{name}|px2^{int(round(math.log2(max(px, 1))))}|q2^{int(round(math.log2(max(num_quads, 1))))}|c{color_mode}"
+
+
+def _load_cache():
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _save_cache(c):
+    p = cache_path()
+    os.makedirs(os.path.dirname(p), exist_ok=True)
+    tmp = p + f".{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(c, f, indent=1, sort_keys=True)
+    os.replace(tmp, p)
+
+
+def lookup(width, height, num_quads, color_mode, device=None):
+    return _load_cache().get(workload_key(width, height, num_quads, color_mode, device))
+
+
+def tune(scene, width: int, height: int, ks=DEFAULT_KS, ctas_per_sm=(0,), reps: int = 5,
+         use_cache: bool = True, device=None):
+    """scene: a DeviceScene. Returns {'sorter_k', 'raster_ctas_per_sm', 'ms', 'table'}."""
+    from . import Renderer
+    key = workload_key(width, height, scene.num_quads, scene.color_mode, device)
+    cache = _load_cache() if use_cache else {}
+    if use_cache and key in cache:
+        return cache[key]
+    table = []
+    ref_img = None
+    for k in ks:
+        for c in ctas_per_sm:
+            r = Renderer(sorter_k=k, raster_ctas_per_sm=c, device=device)
+            out = r.make_outputs(width, height)
+            view = r.view_struct(scene, width, height, out)
+            st = r.render_views([view])                    # sizes the workspace, checked
+            img = out["rgba"].clone()
+            if ref_img is None:
+                ref_img = img
+            elif not torch.equal(img, ref_img):
+                raise RuntimeError(f"sorter_k={k} changed the image: the pipeline must be exact")
+            times = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                r.render_views([view], check=False)
+                b.record()
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b))
+            ovf = B_overflow(r)
+            table.append(dict(sorter_k=k, raster_ctas_per_sm=c, ms=statistics.median(times),
+                              overflow_pixels=ovf, fragments=int(st.fragments)))
+            r.close()
+    best = min(table, key=lambda t: t["ms"])
+    result = dict(sorter_k=best["sorter_k"], raster_ctas_per_sm=best["raster_ctas_per_sm"],
+                  ms=best["ms"], table=table)
+    if use_cache:
+        cache[key] = result
+        _save_cache(cache)
+    return result
+
+
+def B_overflow(r) -> int:
+    from . import _binding as B
+    return int(B.lr_get_stats(r.ctx, raise_on_error=False).overflow_pixels)

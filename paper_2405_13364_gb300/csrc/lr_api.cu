@@ -74,7 +74,7 @@ static const RasterVariant kVariants[] = {
 
 struct Layout {
   size_t ctrl, views, rec_xy, rec_q, rec_rect, rec_info, bin_count, bin_off, bin_cursor, bin_order;
-  size_t refs, refs_tmp, ovf_list, total;
+  size_t refs, refs_tmp, ref_hb, ovf_list, total;
   long long total_quads = 0, total_pix = 0, refs_cap = 0;
   int total_bins = 0, total_chunks = 0;
 };
@@ -117,19 +117,21 @@ static long long default_refs(const Layout& L, int ref_factor) {
   return std::min((long long)ref_factor * L.total_quads + 64LL * L.total_bins + 1024, kMaxRefs);
 }
 
+// per reference: the sort key, its merge buffer slot and its half-block mask
 static size_t bytes_for_refs(const Layout& L, long long refs) {
-  return L.refs + align256(sizeof(unsigned long long) * (size_t)refs) * 2;
+  return L.refs + align256(sizeof(unsigned long long) * (size_t)refs) * 2 + align256(sizeof(uint32_t) * (size_t)refs);
 }
 
-// capacity from the bytes available, placing refs_tmp after refs
+// capacity from the bytes available, placing refs_tmp and ref_hb after refs
 static void set_capacity(Layout& L, size_t ws_bytes) {
   long long cap = 0;
-  if (ws_bytes > L.refs) cap = (long long)((ws_bytes - L.refs) / (2 * sizeof(unsigned long long)));
+  if (ws_bytes > L.refs) cap = (long long)((ws_bytes - L.refs) / (2 * sizeof(unsigned long long) + sizeof(uint32_t)));
   cap = std::min(cap, kMaxRefs);
-  cap &= ~31LL;
-  while (cap > 0 && bytes_for_refs(L, cap) > ws_bytes) cap -= 32;
+  cap &= ~63LL;
+  while (cap > 0 && bytes_for_refs(L, cap) > ws_bytes) cap -= 64;
   L.refs_cap = std::max(cap, 0LL);
   L.refs_tmp = L.refs + align256(sizeof(unsigned long long) * (size_t)L.refs_cap);
+  L.ref_hb = L.refs_tmp + align256(sizeof(unsigned long long) * (size_t)L.refs_cap);
   L.total = bytes_for_refs(L, L.refs_cap);
 }
 
@@ -154,6 +156,7 @@ static Ws make_ws(const Layout& L, void* base, int n_views) {
   w.bin_order = reinterpret_cast<uint32_t*>(b + L.bin_order);
   w.refs = reinterpret_cast<unsigned long long*>(b + L.refs);
   w.refs_tmp = reinterpret_cast<unsigned long long*>(b + L.refs_tmp);
+  w.ref_hb = reinterpret_cast<uint32_t*>(b + L.ref_hb);
   w.ovf_list = reinterpret_cast<uint32_t*>(b + L.ovf_list);
   return w;
 }
@@ -284,6 +287,8 @@ static lr_status check_view(lr_ctx* c, const lr_view& v) {
   return LR_OK;
 }
 
+lr_status lr_internal_check_view(lr_ctx* ctx, const lr_view* view) { return check_view(ctx, *view); }
+
 static lr_status layout_for(lr_ctx* c, int n, const lr_view* views, Layout* out) {
   std::vector<long long> Q(n);
   std::vector<int> W(n), H(n);
@@ -358,29 +363,20 @@ struct BwdArgs {
   float* grad_colors;
 };
 
-static lr_status enqueue(lr_ctx* ctx, int32_t n_views, const lr_view* views, void* workspace,
-                         size_t workspace_bytes, lr_stream stream, const BwdArgs* bwd) {
-  if (!ctx) return LR_ERR_INVALID_ARG;
-  if (n_views <= 0 || !views) return fail(ctx, LR_ERR_INVALID_ARG, "need at least one view%s");
-  if (!workspace || !aligned(workspace, 256)) return fail(ctx, LR_ERR_INVALID_ARG, "workspace must be non-null and 256-byte aligned%s");
-  for (int i = 0; i < n_views; ++i) {
-    lr_status s = check_view(ctx, views[i]);
-    if (s != LR_OK) return s;
-  }
+// A render, checked and laid out on the host: workspace pointers and view descriptors.
+struct Prepared {
   Layout L;
-  lr_status s = layout_for(ctx, n_views, views, &L);
-  if (s != LR_OK) return s;
-  set_capacity(L, workspace_bytes);
-  if (L.refs_cap < 1024) return fail(ctx, LR_ERR_OOM, "workspace too small (see lr_workspace_size)%s");
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaSetDevice(ctx->device);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  std::vector<ViewDev> vd;
+  bool any_vertex = false;
+  Ws ws;
+  ViewDev* views_dev = nullptr;
+};
 
-  // ---- view descriptors ---------------------------------------------------------------
-  std::vector<ViewDev> vd(n_views);
+static void describe_views(int32_t n_views, const lr_view* views, std::vector<ViewDev>& vd, bool* any_vertex) {
+  vd.resize(n_views);
   long long qb = 0, pb = 0;
   int bb = 0, cb = 0;
-  bool any_vertex = false;
+  *any_vertex = false;
   for (int i = 0; i < n_views; ++i) {
     const lr_view& v = views[i];
     ViewDev& d = vd[i];
@@ -417,39 +413,68 @@ static lr_status enqueue(lr_ctx* ctx, int32_t n_views, const lr_view* views, voi
     pb += (long long)v.width * v.height;
     bb += d.nbx * d.nby;
     cb += (int)((v.quads.num_quads + kChunkQuads - 1) / kChunkQuads);
-    any_vertex |= (v.quads.color_mode == LR_COLOR_VERTEX && v.quads.num_quads > 0);
+    *any_vertex |= (v.quads.color_mode == LR_COLOR_VERTEX && v.quads.num_quads > 0);
   }
-  Ws ws = make_ws(L, workspace, n_views);
+}
+
+static lr_status prepare(lr_ctx* ctx, int32_t n_views, const lr_view* views, void* workspace,
+                         size_t workspace_bytes, Prepared* P) {
+  if (n_views <= 0 || !views) return fail(ctx, LR_ERR_INVALID_ARG, "need at least one view%s");
+  if (!workspace || !aligned(workspace, 256)) return fail(ctx, LR_ERR_INVALID_ARG, "workspace must be non-null and 256-byte aligned%s");
+  for (int i = 0; i < n_views; ++i) {
+    lr_status s = check_view(ctx, views[i]);
+    if (s != LR_OK) return s;
+  }
+  lr_status s = layout_for(ctx, n_views, views, &P->L);
+  if (s != LR_OK) return s;
+  set_capacity(P->L, workspace_bytes);
+  if (P->L.refs_cap < 1024) return fail(ctx, LR_ERR_OOM, "workspace too small (see lr_workspace_size)%s");
+  describe_views(n_views, views, P->vd, &P->any_vertex);
+  P->ws = make_ws(P->L, workspace, n_views);
+  P->views_dev = reinterpret_cast<ViewDev*>(static_cast<char*>(workspace) + P->L.views);
+  return LR_OK;
+}
+
+// The launch sequence. View descriptors come from kernel parameters (k_write_views) or,
+// when staging is given, from a copy out of pinned host memory (graph replays).
+static lr_status launch_sequence(lr_ctx* ctx, const Prepared& P, cudaStream_t st, const BwdArgs* bwd, bool timed,
+                                 const ViewDev* staging) {
+  const Layout& L = P.L;
+  Ws ws = P.ws;
   if (bwd) {
     ws.fwd = bwd->fwd;
     ws.grad_out = bwd->grad_out;
     ws.grad_col = bwd->grad_colors;
   }
-  ViewDev* views_dev = reinterpret_cast<ViewDev*>(static_cast<char*>(workspace) + L.views);
-  const bool timed = (ctx->cfg.flags & LR_FLAG_TIMING) != 0;
+  const int n_views = ws.n_views;
   rec(ctx, timed, 0, st);
-  for (int first = 0; first < n_views; first += kViewsPerLaunch) {
-    ViewChunk chunk;
-    memset(&chunk, 0, sizeof(chunk));
-    chunk.first = first;
-    chunk.count = std::min(kViewsPerLaunch, n_views - first);
-    for (int i = 0; i < chunk.count; ++i) chunk.v[i] = vd[first + i];
-    k_write_views<<<1, 32, 0, st>>>(chunk, views_dev);
+  if (staging) {
+    cudaError_t e = cudaMemcpyAsync(P.views_dev, staging, sizeof(ViewDev) * (size_t)n_views, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "view descriptor copy");
+  } else {
+    for (int first = 0; first < n_views; first += kViewsPerLaunch) {
+      ViewChunk chunk;
+      memset(&chunk, 0, sizeof(chunk));
+      chunk.first = first;
+      chunk.count = std::min(kViewsPerLaunch, n_views - first);
+      for (int i = 0; i < chunk.count; ++i) chunk.v[i] = P.vd[first + i];
+      k_write_views<<<1, 32, 0, st>>>(chunk, P.views_dev);
+    }
   }
   k_init<<<std::max(1, (L.total_bins + 255) / 256), 256, 0, st>>>(ws, (unsigned long long)L.refs_cap);
   if (L.total_quads > 0) k_setup<<<(unsigned)((L.total_quads + 255) / 256), 256, 0, st>>>(ws);
   rec(ctx, timed, 1, st);
-  if (L.total_chunks > 0) k_bin_count<<<L.total_chunks, 512, 0, st>>>(ws);
+  if (L.total_chunks > 0) k_bin_count<<<L.total_chunks, kBinThreads, 0, st>>>(ws);
   rec(ctx, timed, 2, st);
   k_bin_scan<<<1, 1024, 0, st>>>(ws);
   rec(ctx, timed, 3, st);
-  if (L.total_chunks > 0) k_bin_scatter<<<L.total_chunks, 512, 0, st>>>(ws);
+  if (L.total_chunks > 0) k_bin_scatter<<<L.total_chunks, kBinThreads, 0, st>>>(ws);
   rec(ctx, timed, 4, st);
   k_bin_sort<<<L.total_bins, 256, kSortSmemCap * sizeof(unsigned long long), st>>>(ws);
   rec(ctx, timed, 5, st);
-  const int mode = bwd ? 2 : (any_vertex ? 1 : 0);
-  const int rblocks = bwd ? ctx->raster_blocks_bwd : (any_vertex ? ctx->raster_blocks_vtx : ctx->raster_blocks_flat);
-  e = ctx->variant->launch(mode, ws, ctx->sms * rblocks, st);
+  const int mode = bwd ? 2 : (P.any_vertex ? 1 : 0);
+  const int rblocks = bwd ? ctx->raster_blocks_bwd : (P.any_vertex ? ctx->raster_blocks_vtx : ctx->raster_blocks_flat);
+  cudaError_t e = ctx->variant->launch(mode, ws, ctx->sms * rblocks, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "raster launch");
   rec(ctx, timed, 6, st);
   e = launch_overflow(bwd != nullptr, ws, ctx->sms * ctx->ovf_blocks, st);
@@ -457,13 +482,137 @@ static lr_status enqueue(lr_ctx* ctx, int32_t n_views, const lr_view* views, voi
   rec(ctx, timed, 7, st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+  return LR_OK;
+}
+
+static void remember_last(lr_ctx* ctx, const Prepared& P, cudaStream_t st, void* workspace, bool timed) {
   ctx->last_stream = st;
   ctx->last_ws = workspace;
-  ctx->last_views = n_views;
-  ctx->last_quads = L.total_quads;
-  ctx->last_cap = L.refs_cap;
+  ctx->last_views = P.ws.n_views;
+  ctx->last_quads = P.L.total_quads;
+  ctx->last_cap = P.L.refs_cap;
   ctx->have_last = true;
   ctx->last_timed = timed;
+}
+
+static lr_status enqueue(lr_ctx* ctx, int32_t n_views, const lr_view* views, void* workspace,
+                         size_t workspace_bytes, lr_stream stream, const BwdArgs* bwd) {
+  if (!ctx) return LR_ERR_INVALID_ARG;
+  Prepared P;
+  lr_status s = prepare(ctx, n_views, views, workspace, workspace_bytes, &P);
+  if (s != LR_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  const bool timed = (ctx->cfg.flags & LR_FLAG_TIMING) != 0;
+  s = launch_sequence(ctx, P, st, bwd, timed, nullptr);
+  if (s != LR_OK) return s;
+  remember_last(ctx, P, st, workspace, timed);
+  return LR_OK;
+}
+
+// ---- captured batches (CUDA graphs) ------------------------------------------------------
+
+struct lr_graph {
+  lr_ctx* ctx = nullptr;
+  void* ws = nullptr;
+  size_t bytes = 0;
+  Prepared P;
+  std::vector<lr_view> shape;        // the views the graph was made for
+  ViewDev* staging[2] = {nullptr, nullptr};   // pinned; read by each replay's first node
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaEvent_t done[2] = {nullptr, nullptr};
+  bool launched[2] = {false, false};
+  int next = 0;
+};
+
+static void free_graph(lr_graph* g) {
+  for (int b = 0; b < 2; ++b) {
+    if (g->done[b]) { cudaEventSynchronize(g->done[b]); cudaEventDestroy(g->done[b]); }
+    if (g->exec[b]) cudaGraphExecDestroy(g->exec[b]);
+    if (g->staging[b]) cudaFreeHost(g->staging[b]);
+  }
+  delete g;
+}
+
+extern "C" lr_status lr_graph_create(lr_ctx* ctx, int32_t n_views, const lr_view* views, void* workspace,
+                                     size_t workspace_bytes, lr_graph** out) {
+  if (!ctx || !out) return LR_ERR_INVALID_ARG;
+  *out = nullptr;
+  lr_graph* g = new (std::nothrow) lr_graph();
+  if (!g) return LR_ERR_OOM;
+  g->ctx = ctx;
+  g->ws = workspace;
+  g->bytes = workspace_bytes;
+  lr_status s = prepare(ctx, n_views, views, workspace, workspace_bytes, &g->P);
+  if (s != LR_OK) { delete g; return s; }
+  g->shape.assign(views, views + n_views);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  cudaStream_t cap = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    e = cudaMallocHost(reinterpret_cast<void**>(&g->staging[b]), sizeof(ViewDev) * (size_t)n_views);
+    if (e != cudaSuccess) break;
+    memcpy(g->staging[b], g->P.vd.data(), sizeof(ViewDev) * (size_t)n_views);
+    e = cudaEventCreateWithFlags(&g->done[b], cudaEventDisableTiming);
+    if (e != cudaSuccess) break;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    s = launch_sequence(ctx, g->P, cap, nullptr, false, g->staging[b]);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(cap, &graph);
+    if (s != LR_OK || ee != cudaSuccess) { e = ee != cudaSuccess ? ee : cudaErrorUnknown; if (graph) cudaGraphDestroy(graph); break; }
+    e = cudaGraphInstantiate(&g->exec[b], graph, 0);
+    cudaGraphDestroy(graph);
+  }
+  if (cap) cudaStreamDestroy(cap);
+  if (e != cudaSuccess || s != LR_OK) {
+    lr_status r = s != LR_OK ? s : cuda_fail(ctx, e, "graph capture");
+    free_graph(g);
+    return r;
+  }
+  *out = g;
+  return LR_OK;
+}
+
+extern "C" lr_status lr_graph_launch(lr_graph* g, const lr_view* views, lr_stream stream) {
+  if (!g) return LR_ERR_INVALID_ARG;
+  lr_ctx* ctx = g->ctx;
+  const int n = g->P.ws.n_views;
+  const int b = g->next;
+  if (g->launched[b]) {
+    // the replay that last read this staging buffer must have copied it
+    cudaError_t e = cudaEventSynchronize(g->done[b]);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventSynchronize");
+  }
+  if (views) {
+    for (int i = 0; i < n; ++i) {
+      const lr_view& a = views[i];
+      const lr_view& s0 = g->shape[i];
+      if (a.width != s0.width || a.height != s0.height || a.quads.num_quads != s0.quads.num_quads ||
+          a.quads.color_mode != s0.quads.color_mode)
+        return fail(ctx, LR_ERR_INVALID_ARG, "graph launch views must keep the captured shapes%s");
+      lr_status s = check_view(ctx, a);
+      if (s != LR_OK) return s;
+    }
+    std::vector<ViewDev> vd;
+    bool any_vertex = false;
+    describe_views(n, views, vd, &any_vertex);
+    memcpy(g->staging[b], vd.data(), sizeof(ViewDev) * (size_t)n);
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaGraphLaunch(g->exec[b], st);
+  if (e == cudaSuccess) e = cudaEventRecord(g->done[b], st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+  g->launched[b] = true;
+  g->next = b ^ 1;
+  remember_last(ctx, g->P, st, g->ws, false);
+  return LR_OK;
+}
+
+extern "C" lr_status lr_graph_destroy(lr_graph* g) {
+  if (!g) return LR_ERR_INVALID_ARG;
+  free_graph(g);
   return LR_OK;
 }
 

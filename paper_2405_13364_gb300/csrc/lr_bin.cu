@@ -1,12 +1,13 @@
 // lr_bin.cu -- Stage 2 of the pipeline, quad binning (Sec. 2, "Stage 2: quad binning"),
 // plus the per-bin depth sort that feeds Stage 3.
 //
-//   k_bin_count    Phase 1: per-bin reference counts. Each CTA owns a chunk of 4096 quads
+//   k_bin_count    Phase 1: per-bin reference counts. Each CTA owns a chunk of 1024 quads
 //                  of one view and counts into shared-memory bin counters (the paper's
 //                  5120-entry arrays), then adds its non-zero counters to global memory.
-//                  Small quads (bin rectangle <= 2x2) are counted from their AABB; large
-//                  quads are tested bin by bin with a conservative per-triangle edge test
-//                  (trivial reject), the whole warp sharing one large quad's bins.
+//                  Quads whose bin rectangle is at most 4x4 bins are counted from their
+//                  AABB; larger quads are tested bin by bin with a conservative
+//                  per-triangle edge test (trivial reject), the whole warp sharing one
+//                  large quad's bins.
 //   k_bin_scan     Phase 2: exclusive scan of the counts into list offsets, capacity
 //                  check, and a categorisation of bins by size (the paper's empty / low /
 //                  high) that orders the rasteriser's work queue, largest bins first.
@@ -131,7 +132,7 @@ __device__ __forceinline__ void for_each_ref(const Ws& ws, const ViewDev& V, lon
   }
 }
 
-__global__ __launch_bounds__(512) void k_bin_count(Ws ws) {
+__global__ __launch_bounds__(kBinThreads) void k_bin_count(Ws ws) {
   __shared__ uint32_t hist[kHistSmemBins];
   const int v = view_of_chunk(ws.views, ws.n_views, blockIdx.x);
   const ViewDev& V = ws.views[v];
@@ -234,7 +235,7 @@ __global__ __launch_bounds__(1024) void k_bin_scan(Ws ws) {
   }
 }
 
-__global__ __launch_bounds__(512) void k_bin_scatter(Ws ws) {
+__global__ __launch_bounds__(kBinThreads) void k_bin_scatter(Ws ws) {
   __shared__ uint32_t hist[kHistSmemBins];
   if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
   const int v = view_of_chunk(ws.views, ws.n_views, blockIdx.x);
@@ -301,14 +302,42 @@ __device__ void cta_merge(const unsigned long long* a, int na, const unsigned lo
   }
 }
 
+// For every sorted reference of a bin, the 32-bit mask of the bin's 8x4 half-blocks
+// (bit hy * 4 + hx) that the quad's pixel AABB overlaps; the rasteriser's per-half-block
+// filter then tests one bit instead of gathering the quad's rectangle.
+__device__ void write_hb_masks(const Ws& ws, const unsigned long long* r, uint32_t* hb, int n, int bin) {
+  const int v = view_of_bin(ws.views, ws.n_views, bin);
+  const ViewDev& V = ws.views[v];
+  const int b = bin - V.bin_base;
+  const int x0 = (b % V.nbx) << kBinLog2, y0 = (b / V.nbx) << kBinLog2;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const uint32_t rec = ~(uint32_t)r[i];
+    uint32_t mask = 0;
+    if (rec < (uint64_t)ws.total_quads) {
+      const uint2 rc = ws.rec_rect[rec];
+      const int px0 = max((int)(rc.x & 0xffff), x0) - x0, px1 = min((int)(rc.x >> 16), x0 + kBin - 1) - x0;
+      const int py0 = max((int)(rc.y & 0xffff), y0) - y0, py1 = min((int)(rc.y >> 16), y0 + kBin - 1) - y0;
+      if (px0 <= px1 && py0 <= py1) {
+        const int hx0 = px0 / kHbW, hx1 = px1 / kHbW, hy0 = py0 / kHbH, hy1 = py1 / kHbH;
+        const uint32_t row = ((2u << hx1) - 1u) & ~((1u << hx0) - 1u);
+        for (int hy = hy0; hy <= hy1; ++hy) mask |= row << (hy * (kBin / kHbW));
+      }
+    }
+    hb[i] = mask;
+  }
+}
+
 __global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {
   extern __shared__ unsigned long long sbuf[];
   if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
   const int bin = blockIdx.x;
   const uint32_t off = ws.bin_off[bin];
   const int n = (int)(ws.bin_off[bin + 1] - off);
-  if (n <= 1) return;
   unsigned long long* r = ws.refs + off;
+  if (n <= 1) {
+    write_hb_masks(ws, r, ws.ref_hb + off, n, bin);
+    return;
+  }
   if (n <= kSortSmemCap) {
     int n2 = 32;
     while (n2 < n) n2 <<= 1;
@@ -316,6 +345,8 @@ __global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {
     __syncthreads();
     smem_bitonic_sort(sbuf, n2);
     for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = sbuf[i];
+    __syncthreads();
+    write_hb_masks(ws, r, ws.ref_hb + off, n, bin);
     return;
   }
   // high-density bin: sort runs of kSortSmemCap in shared memory, then merge in global
@@ -341,6 +372,8 @@ __global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {
   if (src != r) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = src[i];
   }
+  __syncthreads();
+  write_hb_masks(ws, r, ws.ref_hb + off, n, bin);
 }
 
 }  // namespace lr

@@ -20,7 +20,9 @@ constexpr int kHbPerBin = (kBin / kHbW) * (kBin / kHbH);   // 32
 constexpr float kGuardPx = 16384.0f;        // guard band, pixels
 constexpr int kSortSmemCap = 4096;          // bins up to this many refs sort in shared memory
 constexpr int kHistSmemBins = 5120;         // shared-memory bin counters per CTA (Sec. 2 Stage 2)
-constexpr int kChunkQuads = 4096;           // quads per binning CTA
+constexpr int kChunkQuads = 1024;           // quads per binning CTA
+constexpr int kBinThreads = 256;            // threads per binning CTA
+constexpr int kSmallBins = 4;               // AABB-counted up to kSmallBins x kSmallBins bins
 
 // cull reasons (stats and rec_info bits 8..11)
 enum Cull : uint32_t {
@@ -31,7 +33,7 @@ enum Cull : uint32_t {
 // rec_info bits
 constexpr uint32_t kInfoTri0 = 1u;          // triangle 0 has non-zero area
 constexpr uint32_t kInfoTri1 = 2u;          // triangle 1 has non-zero area
-constexpr uint32_t kInfoLarge = 4u;         // bin rectangle larger than 2x2 bins
+constexpr uint32_t kInfoLarge = 4u;         // bin rectangle larger than kSmallBins^2 bins
 constexpr uint32_t kRectInvisible = 0x0000FFFFu;   // rect.x value of a culled quad
 
 struct ViewDev {
@@ -95,6 +97,7 @@ struct Ws {
   uint32_t* bin_order;       // [total_bins]: bins by decreasing reference count
   unsigned long long* refs;      // [refs_cap] sorted per bin: (~rep_bits << 32) | ~record
   unsigned long long* refs_tmp;  // [refs_cap] merge buffer of the high-density sort
+  uint32_t* ref_hb;          // [refs_cap] half-blocks of its bin that reference i's AABB overlaps
   uint32_t* ovf_list;        // [total_pix] flattened pixel ids registered for the exact path
   // backward
   const float* grad_out;     // f32[H][W][4] of view 0

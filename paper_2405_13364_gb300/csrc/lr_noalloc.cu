@@ -102,12 +102,13 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
   const size_t o_ord = o; o = up256(o + 4 * (size_t)nbins);
   const size_t o_ovf = o; o = up256(o + 4 * (size_t)npix);
   if (o >= (size_t)LR_NOALLOC_SCRATCH_BYTES) return LR_ERR_TOO_LARGE;
-  long long cap = (long long)(((size_t)LR_NOALLOC_SCRATCH_BYTES - o - 512) / 16) & ~31LL;
+  long long cap = (long long)(((size_t)LR_NOALLOC_SCRATCH_BYTES - o - 1024) / 20) & ~63LL;
   if (cap > 0xFFFFFF00LL) cap = 0xFFFFFF00LL;
   // require room for at least two references per quad and one per bin
   if (cap < 2 * Q + nbins + 1024) return LR_ERR_TOO_LARGE;
   const size_t o_refs = o;
   const size_t o_tmp = up256(o_refs + 8 * (size_t)cap);
+  const size_t o_hb = up256(o_tmp + 8 * (size_t)cap);
 
   // ---- per-device set-up (first call on this device only) ------------------------------
   int dev = 0;
@@ -178,6 +179,7 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
   ws.bin_order = reinterpret_cast<uint32_t*>(base + o_ord);
   ws.refs = reinterpret_cast<unsigned long long*>(base + o_refs);
   ws.refs_tmp = reinterpret_cast<unsigned long long*>(base + o_tmp);
+  ws.ref_hb = reinterpret_cast<uint32_t*>(base + o_hb);
   ws.ovf_list = reinterpret_cast<uint32_t*>(base + o_ovf);
 
   // ---- the pipeline, as lr_render launches it ------------------------------------------
@@ -186,9 +188,9 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
   k_noalloc_view<<<1, 1, 0, st>>>(v, reinterpret_cast<ViewDev*>(base + o_view));
   k_init<<<(int)((nbins + 255) / 256), 256, 0, st>>>(ws, (unsigned long long)cap);
   if (Q > 0) k_setup<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(ws);
-  if (chunks > 0) k_bin_count<<<chunks, 512, 0, st>>>(ws);
+  if (chunks > 0) k_bin_count<<<chunks, kBinThreads, 0, st>>>(ws);
   k_bin_scan<<<1, 1024, 0, st>>>(ws);
-  if (chunks > 0) k_bin_scatter<<<chunks, 512, 0, st>>>(ws);
+  if (chunks > 0) k_bin_scatter<<<chunks, kBinThreads, 0, st>>>(ws);
   k_bin_sort<<<(int)nbins, 256, kSortSmemCap * sizeof(unsigned long long), st>>>(ws);
   const bool vtx = Q > 0 && q.color_mode == LR_COLOR_VERTEX;
   if (launch_raster_3(vtx ? 1 : 0, ws, ds.sms * (vtx ? ds.blocks_vtx : ds.blocks_flat), st) != cudaSuccess)

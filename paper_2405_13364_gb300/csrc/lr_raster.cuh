@@ -8,14 +8,15 @@
 //
 // Per half-block (all from the bin's reference list, already sorted front to back by
 // k_bin_sort -- stage 1 of the two-stage sort):
-//   1. filter: 32 references at a time, test the quad's pixel AABB against the half-block,
-//      and queue the hits in shared memory (order preserved);
+//   1. filter: 32 references at a time, test the reference's half-block bit (precomputed
+//      per reference by k_bin_sort), and queue the hits in shared memory, order preserved;
 //   2. triangle setup, lane-parallel: for 32 queued quads, both triangles' integer edge
 //      functions at the half-block origin, per-pixel steps, 1/area, depth-plane deltas;
 //      a triangle whose edge values stay below 2^30 on the half-block is marked "fast"
-//      and evaluated with 32-bit integers, others with exact 64-bit integers;
-//   3. coverage, warp-uniform loop over the 64 triangles: each lane tests its own pixel
-//      centre (top-left rule) and sets one bit per covering triangle;
+//      and evaluated with 32-bit integers, others with exact 64-bit integers; the same
+//      lane computes each triangle's 32-pixel coverage mask (top-left rule) row by row;
+//   3. coverage, transposed: a 32x32 bit transpose across the warp turns "triangle ->
+//      pixels" into "pixel -> triangles", one bit per covering triangle in each lane;
 //   4. fragments, per lane in queue order: the exact depth key of the fragment
 //      (interpolated 1/w, identical bit for bit to the oracle's formula) is pushed into a
 //      K-slot register sorter (stage 2, the paper's "depth filter"). When full,
@@ -70,41 +71,56 @@ __device__ __forceinline__ void edges64(const TriSm& T, int px, int py, long lon
 // has zero area or its pixel AABB misses the half-block.
 __device__ __forceinline__ bool setup_tri(TriSm& T, const int X[4], const int Y[4], const float qv[4],
                                           uint32_t info, int t, uint32_t jl, int ox, int oy,
-                                          int cor[3]) {
+                                          int cor[3], int box[4], int le[3], int lsx[3], int lsy[3]) {
   if (!(info & (t ? kInfoTri1 : kInfoTri0))) return false;
-  int ia = 0, ib = t ? 2 : 1, ic = t ? 3 : 2;
-  long long A = area2(X[ia], Y[ia], X[ib], Y[ib], X[ic], Y[ic]);
-  if (A < 0) { const int tmp = ib; ib = ic; ic = tmp; A = -A; }
-  const int xmin = min(X[ia], min(X[ib], X[ic])), xmax = max(X[ia], max(X[ib], X[ic]));
-  const int ymin = min(Y[ia], min(Y[ib], Y[ic])), ymax = max(Y[ia], max(Y[ib], Y[ic]));
-  if (ceil_div256((long long)xmin - 128) > ox + kHbW - 1 || floor_div256((long long)xmax - 128) < ox ||
-      ceil_div256((long long)ymin - 128) > oy + kHbH - 1 || floor_div256((long long)ymax - 128) < oy)
-    return false;
-  cor[0] = ia; cor[1] = ib; cor[2] = ic;
-  T.X[0] = X[ia]; T.X[1] = X[ib]; T.X[2] = X[ic];
-  T.Y[0] = Y[ia]; T.Y[1] = Y[ib]; T.Y[2] = Y[ic];
-  T.q0 = qv[ia];
-  T.d1 = __fsub_rn(qv[ib], qv[ia]);
-  T.d2 = __fsub_rn(qv[ic], qv[ia]);
+  // vertices (v0, v1, v2) of T0 or (v0, v2, v3) of T1, chosen with selects (no indexing)
+  int xa = X[0], ya = Y[0];
+  int xb = t ? X[2] : X[1], yb = t ? Y[2] : Y[1];
+  int xc = t ? X[3] : X[2], yc = t ? Y[3] : Y[2];
+  float qa = qv[0], qb = t ? qv[2] : qv[1], qc = t ? qv[3] : qv[2];
+  int ib = t ? 2 : 1, ic = t ? 3 : 2;
+  long long A = area2(xa, ya, xb, yb, xc, yc);
+  if (A < 0) {   // orientation fix: swap v1 and v2
+    int ti = xb; xb = xc; xc = ti;
+    ti = yb; yb = yc; yc = ti;
+    const float tq = qb; qb = qc; qc = tq;
+    ti = ib; ib = ic; ic = ti;
+    A = -A;
+  }
+  const int xmin = min(xa, min(xb, xc)), xmax = max(xa, max(xb, xc));
+  const int ymin = min(ya, min(yb, yc)), ymax = max(ya, max(yb, yc));
+  const int bx0 = ceil_div256((long long)xmin - 128), bx1 = floor_div256((long long)xmax - 128);
+  const int by0 = ceil_div256((long long)ymin - 128), by1 = floor_div256((long long)ymax - 128);
+  if (bx0 > ox + kHbW - 1 || bx1 < ox || by0 > oy + kHbH - 1 || by1 < oy) return false;
+  box[0] = max(bx0 - ox, 0);
+  box[1] = min(bx1 - ox, kHbW - 1);
+  box[2] = max(by0 - oy, 0);
+  box[3] = min(by1 - oy, kHbH - 1);
+  cor[0] = 0; cor[1] = ib; cor[2] = ic;
+  T.X[0] = xa; T.X[1] = xb; T.X[2] = xc;
+  T.Y[0] = ya; T.Y[1] = yb; T.Y[2] = yc;
+  T.q0 = qa;
+  T.d1 = __fsub_rn(qb, qa);
+  T.d2 = __fsub_rn(qc, qa);
   T.inv = __fdiv_rn(1.0f, __ll2float_rn(A));
   T.id = 2u * jl + (uint32_t)t;
   uint32_t flags = kTriValid;
   bool fast = true;
   const long long P0x = 256LL * ox + 128, P0y = 256LL * oy + 128;
   const long long lim = 1LL << 30;
+  // edges v1->v2, v2->v0, v0->v1
+  const int ux[3] = {xb, xc, xa}, uy[3] = {yb, yc, ya}, wx[3] = {xc, xa, xb}, wy[3] = {yc, ya, yb};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const int u = k == 0 ? 1 : (k == 1 ? 2 : 0);
-    const int w = k == 0 ? 2 : (k == 1 ? 0 : 1);
-    const long long dx = (long long)T.X[w] - T.X[u], dy = (long long)T.Y[w] - T.Y[u];
+    const long long dx = (long long)wx[k] - ux[k], dy = (long long)wy[k] - uy[k];
     const bool owned = dy < 0 || (dy == 0 && dx > 0);
-    const long long e0 = dx * (P0y - T.Y[u]) - dy * (P0x - T.X[u]) + (owned ? 0 : -1);
+    const long long e0 = dx * (P0y - uy[k]) - dy * (P0x - ux[k]) + (owned ? 0 : -1);
     const long long sx = -256 * dy, sy = 256 * dx;
     const long long c1 = e0 + (kHbW - 1) * sx, c2 = e0 + (kHbH - 1) * sy, c3 = c1 + (kHbH - 1) * sy;
     fast &= (e0 > -lim && e0 < lim && c1 > -lim && c1 < lim && c2 > -lim && c2 < lim && c3 > -lim && c3 < lim);
-    T.e[k] = (int)e0;
-    T.sx[k] = (int)sx;
-    T.sy[k] = (int)sy;
+    T.e[k] = le[k] = (int)e0;
+    T.sx[k] = lsx[k] = (int)sx;
+    T.sy[k] = lsy[k] = (int)sy;
     if (!owned) flags |= 1u << (3 + k);
   }
   if (fast) flags |= kTriFast;
@@ -123,6 +139,74 @@ struct GradPixel {
   float fr, fg, fb, fT;      // forward colour and transmittance
   float* grad;               // f32[Q][4] of the view
 };
+
+// Columns lx in [0, 8) of one half-block row where an edge is non-negative, as an 8-bit
+// mask, given the edge value r at lx = 0 and its step sx per column. The edge is linear in
+// lx, so the failing columns form a prefix (sx >= 0) or a suffix (sx < 0); mirroring the
+// row turns the suffix into a prefix, whose length is found by a 4-step binary search on
+// exact 32-bit edge values (every value evaluated is a pixel centre of the half-block).
+__device__ __forceinline__ uint32_t row_cover(int r, int sx) {
+  const bool neg = sx < 0;
+  const uint32_t g0 = neg ? (uint32_t)r + 7u * (uint32_t)sx : (uint32_t)r;
+  const uint32_t sa = neg ? 0u - (uint32_t)sx : (uint32_t)sx;
+  int cnt = ((int)(g0 + 3u * sa) < 0) ? 4 : 0;
+  cnt += ((int)(g0 + (uint32_t)(cnt + 1) * sa) < 0) ? 2 : 0;
+  cnt += ((int)(g0 + (uint32_t)cnt * sa) < 0) ? 1 : 0;
+  cnt += (cnt == 7 && (int)(g0 + 7u * sa) < 0) ? 1 : 0;
+  return neg ? (0xFFu >> cnt) : ((0xFFu << cnt) & 0xFFu);
+}
+
+// Coverage of the half-block's 32 pixel centres (bit ly * 8 + lx) by a "fast" triangle:
+// per row the intersection of the three edges' covered columns, limited to the triangle's
+// pixel bounding box.
+__device__ __forceinline__ uint32_t tri_mask_fast(const int e[3], const int sx[3], const int sy[3],
+                                                  const int box[4]) {
+  uint32_t mask = 0;
+#pragma unroll 1
+  for (int ly = 0; ly < kHbH; ++ly) {
+    uint32_t row = 0xFFu;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      row &= row_cover((int)((uint32_t)e[k] + (uint32_t)ly * (uint32_t)sy[k]), sx[k]);
+    mask |= row << (ly * kHbW);
+  }
+  const uint32_t cols = ((2u << box[1]) - 1u) & ~((1u << box[0]) - 1u);
+  uint32_t rows = 0;
+#pragma unroll
+  for (int ly = 0; ly < kHbH; ++ly) rows |= (ly >= box[2] && ly <= box[3]) ? (cols << (ly * kHbW)) : 0u;
+  return mask & rows;
+}
+
+// The same with exact 64-bit edge values, pixel by pixel (large triangles).
+static __device__ __noinline__ uint32_t tri_mask_slow(const TriSm& T, int ox, int oy, const int box[4]) {
+  uint32_t mask = 0;
+  for (int ly = box[2]; ly <= box[3]; ++ly)
+    for (int lx = box[0]; lx <= box[1]; ++lx) {
+      long long e[3];
+      edges64(T, ox + lx, oy + ly, e);
+      bool cov = true;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const bool owned = !(T.flags & (1u << (3 + k)));
+        cov &= e[k] > 0 || (e[k] == 0 && owned);
+      }
+      if (cov) mask |= 1u << (ly * kHbW + lx);
+    }
+  return mask;
+}
+
+// 32x32 bit-matrix transpose across a warp: lane r holds row r on entry (bit c = element
+// (r, c)) and column r on exit (bit c = element (c, r)); five butterfly exchanges.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+  const uint32_t m[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int j = 16 >> i;
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? ((x & ~m[i]) | ((y >> j) & m[i])) : ((x & m[i]) | ((y & m[i]) << j));
+  }
+  return x;
+}
 
 template <int K, bool VTX, bool BWD = false>
 struct PixelState {
@@ -263,7 +347,8 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster(Ws ws) {
     unsigned long long hsh = 0;
 
     auto process = [&](int nc) {
-      // ---- 2. triangle setup, one quad per lane ------------------------------------
+      // ---- 2. triangle setup and coverage masks, one quad per lane ---------------------
+      uint32_t tm0 = 0, tm1 = 0;
       if (lane < nc) {
         const uint32_t rec = cand[lane];
         const int4 A = ws.rec_xy[2ull * rec], B = ws.rec_xy[2ull * rec + 1];
@@ -272,14 +357,16 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster(Ws ws) {
         const int X[4] = {A.x, A.z, B.x, B.z}, Y[4] = {A.y, A.w, B.y, B.w};
         const float qv[4] = {Qv.x, Qv.y, Qv.z, Qv.w};
         const uint32_t jl = (uint32_t)(rec - V.quad_base);
-#pragma unroll
+#pragma unroll 1
         for (int t = 0; t < 2; ++t) {
           TriSm& T = tris[2 * lane + t];
-          int cor[3];
-          if (!setup_tri(T, X, Y, qv, info, t, jl, ox, oy, cor)) {
+          int cor[3], box[4], le[3], lsx[3], lsy[3];
+          if (!setup_tri(T, X, Y, qv, info, t, jl, ox, oy, cor, box, le, lsx, lsy)) {
             T.flags = 0;
             continue;
           }
+          const uint32_t mk = (T.flags & kTriFast) ? tri_mask_fast(le, lsx, lsy, box) : tri_mask_slow(T, ox, oy, box);
+          if (t == 0) tm0 = mk; else tm1 = mk;
           if (VTX) {
             float4* qc = qcs + (2 * lane + t) * 3;
             if (!vtx_view) {
@@ -289,11 +376,12 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster(Ws ws) {
               uint4 vi;
               if (V.idx) vi = __ldg(reinterpret_cast<const uint4*>(V.idx) + jl);
               else vi = make_uint4(4 * jl, 4 * jl + 1, 4 * jl + 2, 4 * jl + 3);
-              const uint32_t vids[4] = {vi.x, vi.y, vi.z, vi.w};
 #pragma unroll
               for (int k = 0; k < 3; ++k) {
-                const float4 cc = __ldg(reinterpret_cast<const float4*>(V.col) + vids[cor[k]]);
-                const float qk = qv[cor[k]];
+                const int ck = cor[k];
+                const uint32_t vid = ck == 0 ? vi.x : (ck == 1 ? vi.y : (ck == 2 ? vi.z : vi.w));
+                const float qk = ck == 0 ? qv[0] : (ck == 1 ? qv[1] : (ck == 2 ? qv[2] : qv[3]));
+                const float4 cc = __ldg(reinterpret_cast<const float4*>(V.col) + vid);
                 qc[k] = make_float4(qk * cc.x, qk * cc.y, qk * cc.z, qk * cc.w);
               }
             }
@@ -301,41 +389,15 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster(Ws ws) {
         }
       }
       __syncwarp();
-      // ---- 3. coverage: one bit per covering triangle --------------------------------
-      uint32_t m0 = 0, m1 = 0;
-      for (int c = 0; c < nc; ++c) {
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          const TriSm& T = tris[2 * c + t];
-          const uint32_t fl = T.flags;
-          if (!(fl & kTriValid)) continue;
-          bool cov;
-          if (fl & kTriFast) {
-            const int e0 = (int)((uint32_t)T.e[0] + (uint32_t)lx * (uint32_t)T.sx[0] + (uint32_t)ly * (uint32_t)T.sy[0]);
-            const int e1 = (int)((uint32_t)T.e[1] + (uint32_t)lx * (uint32_t)T.sx[1] + (uint32_t)ly * (uint32_t)T.sy[1]);
-            const int e2 = (int)((uint32_t)T.e[2] + (uint32_t)lx * (uint32_t)T.sx[2] + (uint32_t)ly * (uint32_t)T.sy[2]);
-            cov = (e0 | e1 | e2) >= 0;
-          } else {
-            long long e[3];
-            edges64(T, px, py, e);
-            cov = true;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-              const bool owned = !(fl & (1u << (3 + k)));
-              cov &= e[k] > 0 || (e[k] == 0 && owned);
-            }
-          }
-          cov &= pix_ok;
-          if (t == 0) m0 |= (uint32_t)cov << c;
-          else m1 |= (uint32_t)cov << c;
-        }
-      }
+      // ---- 3. transpose: lane = pixel, bit c = covered by triangle t of quad c -----------
+      uint32_t m0 = warp_transpose32(tm0, lane), m1 = warp_transpose32(tm1, lane);
+      if (!pix_ok) m0 = m1 = 0;
       // ---- 4. fragments in queue order through the K-slot sorter ---------------------
       uint32_t bits = m0 | m1;
       while (bits) {
         const int c = __ffs(bits) - 1;
         bits &= bits - 1;
-#pragma unroll
+#pragma unroll 1
         for (int t = 0; t < 2; ++t) {
           if (!(((t ? m1 : m0) >> c) & 1u)) continue;
           const TriSm& T = tris[2 * c + t];
@@ -402,11 +464,7 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster(Ws ws) {
       uint32_t rec = 0;
       if (i < n) {
         rec = ~(uint32_t)ws.refs[off + i];
-        if (rec < (uint64_t)ws.total_quads) {
-          const uint2 r = ws.rec_rect[rec];
-          hit = (int)(r.x & 0xffff) <= ox + kHbW - 1 && (int)(r.x >> 16) >= ox &&
-                (int)(r.y & 0xffff) <= oy + kHbH - 1 && (int)(r.y >> 16) >= oy;
-        }
+        hit = ((ws.ref_hb[off + i] >> hb) & 1u) && rec < (uint64_t)ws.total_quads;
       }
       const unsigned m = __ballot_sync(0xffffffffu, hit);
       if (hit) cand[qn + __popc(m & ((1u << lane) - 1u))] = rec;

@@ -236,6 +236,9 @@ extern "C" lr_status lr_submit(lr_ctx* ctx, const lr_view* view, uint64_t* ticke
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stopping) return LR_ERR_INVALID_ARG;
+    // reject a malformed request here, so that it cannot fail the batch it would join
+    const lr_status chk = lr_internal_check_view(s->inner, view);
+    if (chk != LR_OK) return chk;
     const uint64_t t = s->next_ticket++;
     Req r;
     r.view = *view;

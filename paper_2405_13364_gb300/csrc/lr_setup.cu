@@ -121,7 +121,7 @@ __global__ __launch_bounds__(256) void k_setup(Ws ws) {
           rect = make_uint2((uint32_t)px0 | ((uint32_t)px1 << 16), (uint32_t)py0 | ((uint32_t)py1 << 16));
           const int bw = (px1 >> kBinLog2) - (px0 >> kBinLog2) + 1;
           const int bh = (py1 >> kBinLog2) - (py0 >> kBinLog2) + 1;
-          if (bw > 2 || bh > 2) info |= kInfoLarge;
+          if (bw > kSmallBins || bh > kSmallBins) info |= kInfoLarge;
         }
       }
     }
