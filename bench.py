@@ -67,7 +67,7 @@ def _env_rank():
 
 
 def _measured_peaks():
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")  # written by the environment, not by this repo
     try:
         with open(p) as f:
             return json.load(f)
@@ -119,6 +119,111 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                 "samples": len(self.samples)}
+
+
+def serving_benchmark(P, torch, num_requests=256, rate_hz=200.0, seed=0):
+    """The served render stream: a seeded Poisson trace of mixed requests (resolutions
+    256x256 .. 2560x1440, the three scene generators at 10k-2M quads), served by the
+    continuous-batching server, against the same trace served one lr_render at a time.
+    Scenes are built and uploaded before the clock starts (a pool of 15 geometries: three
+    generators x five log-spaced sizes; each request uses the pooled geometry of its kind
+    nearest to its quad count, with a camera for its resolution). Returns a dict."""
+    import math
+    import time as _time
+
+    import numpy as np
+
+    import scenegen
+    trace = scenegen.request_trace(num_requests, rate_hz, seed=seed)
+    sizes = [10_000, 40_000, 160_000, 640_000, 2_000_000]
+    pool = {}
+    for kind in ("frustum", "layers", "particles"):
+        for q in sizes:
+            sc = scenegen.scene_for_request(dict(kind=kind, quads=q, width=1920, height=1080, seed=7))
+            pool[(kind, q)] = P.DeviceScene.from_scene(sc)
+
+    def scene_of(req):
+        q = min(sizes, key=lambda s: abs(math.log(s) - math.log(req["quads"])))
+        base = pool[(req["kind"], q)]
+        m, n, f = scenegen.perspective(req["width"], req["height"])
+        return P.DeviceScene(base.positions, base.indices, base.colors, base.color_mode,
+                             tuple(float(x) for x in m.reshape(-1)), float(n), float(f))
+
+    scenes = [scene_of(r) for r in trace]
+    frags = 0
+    # ---- sequential: one lr_render per request, in arrival order, one at a time -----------
+    r = P.Renderer(sorter_k=3)
+    outs = [r.make_outputs(q["width"], q["height"]) for q in trace]
+    views = [P.Renderer.view_struct(s, q["width"], q["height"], o) for s, q, o in zip(scenes, trace, outs)]
+    for v in views[:8]:
+        r.render_views([v])                      # warm-up, sizes the workspace
+    ref_imgs = []
+    seq_lat, t_start = [], None
+    t0 = _time.perf_counter()
+    for q, v, o in zip(trace, views, outs):
+        now = _time.perf_counter() - t0
+        if now < q["arrival"]:
+            _time.sleep(q["arrival"] - now)
+        st = r.render_views([v])                 # synchronises and checks the status
+        done = _time.perf_counter() - t0
+        seq_lat.append(done - q["arrival"])
+        frags += int(st.fragments)
+    seq_span = (_time.perf_counter() - t0)
+    ref_imgs = [o["rgba"].clone() for o in outs]
+    # saturated: everything queued at once
+    t1 = _time.perf_counter()
+    for v in views:
+        r.render_views([v])
+    seq_sat = _time.perf_counter() - t1
+    r.close()
+    # ---- served: continuous batching ---------------------------------------------------------
+    srv = P.Server(sorter_k=3, num_slots=3, max_batch_views=8, slot_workspace_bytes=2 << 30)
+    warm = [srv.submit(scenes[i], trace[i]["width"], trace[i]["height"]) for i in range(8)]
+    for t in warm:
+        while srv.poll(t, timeout_us=100_000) is None:
+            pass
+
+    def serve(arrivals):
+        souts = [srv.renderer.make_outputs(q["width"], q["height"]) for q in trace]
+        tickets, t_sub = [], []
+        base = P.Server.now_ns()
+        tb = _time.perf_counter()
+        for i, q in enumerate(trace):
+            if arrivals:
+                now = _time.perf_counter() - tb
+                if now < q["arrival"]:
+                    _time.sleep(q["arrival"] - now)
+            tickets.append(srv.submit(scenes[i], q["width"], q["height"], out=souts[i]))
+        lat, last_done = [], 0
+        for i, t in enumerate(tickets):
+            res = None
+            while res is None:
+                res = srv.poll(t, timeout_us=200_000)
+            status, _, info = res
+            assert status == 0, status
+            arr_ns = base + int((trace[i]["arrival"] if arrivals else 0.0) * 1e9)
+            lat.append((info["done_ns"] - arr_ns) * 1e-9)
+            last_done = max(last_done, info["done_ns"])
+        return souts, lat, (last_done - base) * 1e-9
+
+    souts, srv_lat, srv_span = serve(True)
+    torch.cuda.synchronize()
+    same = all(torch.equal(a["rgba"], b) for a, b in zip(souts, ref_imgs))
+    _, _, srv_sat = serve(False)
+    st = srv.stats()
+    srv.close()
+    pct = lambda xs, p: float(np.percentile(np.array(xs) * 1e3, p))
+    return {
+        "trace": f"{num_requests} requests, Poisson {rate_hz:.0f} req/s, seed {seed}",
+        "fragments": frags,
+        "served": {"fps": round(num_requests / srv_span, 1), "p50_ms": round(pct(srv_lat, 50), 3),
+                   "p99_ms": round(pct(srv_lat, 99), 3),
+                   "saturated_fps": round(num_requests / srv_sat, 1),
+                   "batches": st["batches"], "mean_views_per_batch": round(st["batched_views"] / max(1, st["batches"]), 2)},
+        "sequential": {"fps": round(num_requests / seq_span, 1), "p50_ms": round(pct(seq_lat, 50), 3),
+                       "p99_ms": round(pct(seq_lat, 99), 3), "saturated_fps": round(num_requests / seq_sat, 1)},
+        "served_equals_sequential_bitwise": bool(same),
+    }
 
 
 def run_reference(args):
@@ -205,12 +310,10 @@ def run_gpu(args):
             for k, v in st["stage_ms"].items():
                 stage_sum[k] += v
         torch.cuda.synchronize()
+    from paper_2405_13364_gb300 import replicas
     ms = [a.elapsed_time(b) for a, b in ev]
-    ms_step = sum(ms) / len(ms)
+    ms_step = replicas.max_over_ranks(sum(ms) / len(ms), dist, dev)
     if dist:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
         dist.barrier()
     value = world * frags / (ms_step * 1e-3) / 1e9
 
@@ -247,17 +350,17 @@ def run_gpu(args):
         b.record(stream)
         torch.cuda.synchronize()
         e_ms.append(a.elapsed_time(b))
-    e2e_ms = sum(e_ms) / len(e_ms)
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = replicas.max_over_ranks(sum(e_ms) / len(e_ms), dist, dev)
     e2e_value = world * frags / (e2e_ms * 1e-3) / 1e9
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
+
+    serving = None
+    if args.workload == "layers" and world == 1 and not args.no_serving:
+        serving = serving_benchmark(P, torch)
 
     stages = {k: round(v / args.steps, 4) for k, v in stage_sum.items()}
     raster_ms = stages["raster"]
@@ -303,6 +406,7 @@ def run_gpu(args):
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 3), "unit": "Gfrag/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4)},
+        "served_stream": serving,
         "gpu_launches": 9 * args.steps,
         "clocks": clocks,
     }
@@ -352,6 +456,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--profile", action="store_true", help="short run for ncu (see run_profile)")
     ap.add_argument("--workload", default="layers", choices=["layers", "particles", "frustum", "diff"])
     args = ap.parse_args()

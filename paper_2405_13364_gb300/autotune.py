@@ -1,12 +1,14 @@
 """Autotuner for the rasteriser's launch parameters.
 
 Tunable here: the per-pixel sorter capacity K (the paper's depth-filter size, Sec. 2
-"Sample blending"; every K gives the identical, exact image: a smaller K only sends more
-pixels down the exact overflow path) and the number of persistent rasteriser CTAs per SM.
+"Sample blending") and the number of persistent rasteriser CTAs per SM. Every K gives the
+same coverage and the same exact fragment order; a smaller K only sends more pixels down
+the exact overflow path, whose composite sums in a different order, so colours agree to
+fp32 rounding (the tuner checks 1e-5, the accuracy bar) rather than bit for bit.
 Bin size (32x32) and half-block shape (8x4) are fixed in this build.
 
 The tuner renders the workload with every candidate, checks that all candidates produce
-the same image bit for bit, times each with CUDA events (median of `reps`), and caches the
+the same image within 1e-5, times each with CUDA events (median of `reps`), and caches the
 winner in a JSON file keyed by (GPU name, resolution bucket, quad-count bucket, colour
 mode). The cache path is $LR_AUTOTUNE_CACHE, else ~/.cache/lucidraster_gb300/autotune.json.
 """
@@ -75,8 +77,8 @@ def tune(scene, width: int, height: int, ks=DEFAULT_KS, ctas_per_sm=(0,), reps: 
             img = out["rgba"].clone()
             if ref_img is None:
                 ref_img = img
-            elif not torch.equal(img, ref_img):
-                raise RuntimeError(f"sorter_k={k} changed the image: the pipeline must be exact")
+            elif float((img - ref_img).abs().max()) > 1e-5:
+                raise RuntimeError(f"sorter_k={k} changed the image beyond 1e-5: the pipeline must be exact")
             times = []
             for _ in range(reps):
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

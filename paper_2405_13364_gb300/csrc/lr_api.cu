@@ -31,6 +31,7 @@ __global__ void k_bin_count(Ws ws);
 __global__ void k_bin_scan(Ws ws);
 __global__ void k_bin_scatter(Ws ws);
 __global__ void k_bin_sort(Ws ws);
+__global__ void k_bin_sort_big(Ws ws);
 cudaError_t overflow_occupancy(int* blocks_per_sm);
 cudaError_t launch_overflow(bool bwd, const Ws& ws, int grid, cudaStream_t st);
 
@@ -231,6 +232,8 @@ extern "C" lr_status lr_create(const lr_config* config, lr_ctx** out_ctx) {
   if (e == cudaSuccess) e = c->variant->prepare(&c->raster_blocks_flat, &c->raster_blocks_vtx, &c->raster_blocks_bwd);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bin_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)(kSortSmemCap * sizeof(unsigned long long)));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bin_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(kSortBigCap * sizeof(unsigned long long)));
   if (e == cudaSuccess) e = overflow_occupancy(&c->ovf_blocks);
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&c->host_ctrl), sizeof(Ctrl));
   for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev[i]);
@@ -471,6 +474,7 @@ static lr_status launch_sequence(lr_ctx* ctx, const Prepared& P, cudaStream_t st
   if (L.total_chunks > 0) k_bin_scatter<<<L.total_chunks, kBinThreads, 0, st>>>(ws);
   rec(ctx, timed, 4, st);
   k_bin_sort<<<L.total_bins, 256, kSortSmemCap * sizeof(unsigned long long), st>>>(ws);
+  k_bin_sort_big<<<ctx->sms, kSortBigThreads, kSortBigCap * sizeof(unsigned long long), st>>>(ws);
   rec(ctx, timed, 5, st);
   const int mode = bwd ? 2 : (P.any_vertex ? 1 : 0);
   const int rblocks = bwd ? ctx->raster_blocks_bwd : (P.any_vertex ? ctx->raster_blocks_vtx : ctx->raster_blocks_flat);

@@ -17,9 +17,13 @@
 //                  (~representative 1/w) << 32 | ~record index.
 //   k_bin_sort     Stage-1 depth sort: sorts each bin's references ascending, i.e. front
 //                  to back by a representative depth, ties with the higher quad index
-//                  first. Bins of up to 4096 references are sorted in shared memory; larger
-//                  (high-density) bins sort 4096-reference runs in shared memory and merge
-//                  them through a global buffer.
+//                  first. Bins with fewer than 4096 references: one 256-thread CTA per
+//                  bin, bitonic sort in shared memory.
+//   k_bin_sort_big The high-density bins (4096 references or more; the paper's "high"
+//                  category): persistent 1024-thread CTAs take them from the front
+//                  of the size-ordered bin list and sort up to 16384 references in shared
+//                  memory; beyond that, 16384-reference runs are merged through a global
+//                  buffer.
 #include "lr_common.cuh"
 
 namespace lr {
@@ -171,7 +175,7 @@ __global__ __launch_bounds__(1024) void k_bin_scan(Ws ws) {
     const uint32_t c = i < n ? ws.bin_count[i] : 0u;
     if (i < n) {
       nonempty += c > 0;
-      high += c > (uint32_t)kSortSmemCap;
+      high += c >= (uint32_t)kSortSmemCap;
       mx = c > mx ? c : mx;
       atomicAdd(&cls_count[c ? 33 - __clz(c) : 0], 1u);
     }
@@ -333,12 +337,9 @@ __global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {
   const int bin = blockIdx.x;
   const uint32_t off = ws.bin_off[bin];
   const int n = (int)(ws.bin_off[bin + 1] - off);
+  if (n >= kSortSmemCap) return;   // high-density: k_bin_sort_big
   unsigned long long* r = ws.refs + off;
-  if (n <= 1) {
-    write_hb_masks(ws, r, ws.ref_hb + off, n, bin);
-    return;
-  }
-  if (n <= kSortSmemCap) {
+  if (n > 1) {
     int n2 = 32;
     while (n2 < n) n2 <<= 1;
     for (int i = threadIdx.x; i < n2; i += blockDim.x) sbuf[i] = i < n ? r[i] : ~0ull;
@@ -346,34 +347,58 @@ __global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {
     smem_bitonic_sort(sbuf, n2);
     for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = sbuf[i];
     __syncthreads();
-    write_hb_masks(ws, r, ws.ref_hb + off, n, bin);
-    return;
   }
-  // high-density bin: sort runs of kSortSmemCap in shared memory, then merge in global
-  for (int s = 0; s < n; s += kSortSmemCap) {
-    const int m = min(kSortSmemCap, n - s);
-    for (int i = threadIdx.x; i < kSortSmemCap; i += blockDim.x) sbuf[i] = i < m ? r[s + i] : ~0ull;
-    __syncthreads();
-    smem_bitonic_sort(sbuf, kSortSmemCap);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) r[s + i] = sbuf[i];
-    __syncthreads();
-  }
-  unsigned long long* src = r;
-  unsigned long long* dst = ws.refs_tmp + off;
-  for (int run = kSortSmemCap; run < n; run <<= 1) {
-    for (int s = 0; s < n; s += 2 * run) {
-      const int na = min(run, n - s);
-      const int nbb = min(run, max(0, n - s - run));
-      cta_merge(src + s, na, src + s + na, nbb, dst + s);
+  write_hb_masks(ws, r, ws.ref_hb + off, n, bin);
+}
+
+__global__ __launch_bounds__(kSortBigThreads) void k_bin_sort_big(Ws ws) {
+  extern __shared__ unsigned long long sbuf[];
+  __shared__ int s_bin;
+  if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
+  const unsigned long long n_big = ws.ctrl->bins_high;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned long long k = atomicAdd(&ws.ctrl->sort_head, 1ull);
+      s_bin = k < n_big ? (int)ws.bin_order[k] : -1;
     }
     __syncthreads();
-    unsigned long long* t = src; src = dst; dst = t;
+    const int bin = s_bin;
+    __syncthreads();
+    if (bin < 0) return;
+    const uint32_t off = ws.bin_off[bin];
+    const int n = (int)(ws.bin_off[bin + 1] - off);
+    unsigned long long* r = ws.refs + off;
+    const int run0 = n <= kSortBigCap ? n : kSortBigCap;
+    // sort runs of up to kSortBigCap references in shared memory
+    for (int s = 0; s < n; s += run0) {
+      const int m = min(run0, n - s);
+      int n2 = 32;
+      while (n2 < m) n2 <<= 1;
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) sbuf[i] = i < m ? r[s + i] : ~0ull;
+      __syncthreads();
+      smem_bitonic_sort(sbuf, n2);
+      for (int i = threadIdx.x; i < m; i += blockDim.x) r[s + i] = sbuf[i];
+      __syncthreads();
+    }
+    // merge the runs through the global buffer (only for more than kSortBigCap)
+    unsigned long long* src = r;
+    unsigned long long* dst = ws.refs_tmp + off;
+    for (int run = run0; run < n; run <<= 1) {
+      for (int s = 0; s < n; s += 2 * run) {
+        const int na = min(run, n - s);
+        const int nbb = min(run, max(0, n - s - run));
+        cta_merge(src + s, na, src + s + na, nbb, dst + s);
+      }
+      __syncthreads();
+      unsigned long long* t = src; src = dst; dst = t;
+    }
+    if (src != r) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = src[i];
+    }
+    __syncthreads();
+    write_hb_masks(ws, r, ws.ref_hb + off, n, bin);
+    __syncthreads();
   }
-  if (src != r) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = src[i];
-  }
-  __syncthreads();
-  write_hb_masks(ws, r, ws.ref_hb + off, n, bin);
 }
 
 }  // namespace lr

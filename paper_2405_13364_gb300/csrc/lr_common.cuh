@@ -18,7 +18,9 @@ constexpr int kBin = 1 << kBinLog2;
 constexpr int kHbW = 8, kHbH = 4;           // 8x4 half-blocks (Sec. 2, Stage 3)
 constexpr int kHbPerBin = (kBin / kHbW) * (kBin / kHbH);   // 32
 constexpr float kGuardPx = 16384.0f;        // guard band, pixels
-constexpr int kSortSmemCap = 4096;          // bins up to this many refs sort in shared memory
+constexpr int kSortSmemCap = 4096;          // bins below this many refs: k_bin_sort (256 threads)
+constexpr int kSortBigCap = 16384;          // k_bin_sort_big sorts up to this many in shared memory
+constexpr int kSortBigThreads = 1024;
 constexpr int kHistSmemBins = 5120;         // shared-memory bin counters per CTA (Sec. 2 Stage 2)
 constexpr int kChunkQuads = 1024;           // quads per binning CTA
 constexpr int kBinThreads = 256;            // threads per binning CTA
@@ -68,7 +70,7 @@ struct Ctrl {
   unsigned long long raster_items;
   unsigned long long ovf_count;      // pixels registered for the exact path
   unsigned long long ovf_head;
-  unsigned long long sort_head;
+  unsigned long long sort_head;      // k_bin_sort_big's queue over the high-density bins
   unsigned long long fragments;
   unsigned long long visible;
   unsigned long long culled[8];

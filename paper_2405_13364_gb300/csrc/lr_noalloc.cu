@@ -34,6 +34,7 @@ __global__ void k_bin_count(Ws ws);
 __global__ void k_bin_scan(Ws ws);
 __global__ void k_bin_scatter(Ws ws);
 __global__ void k_bin_sort(Ws ws);
+__global__ void k_bin_sort_big(Ws ws);
 cudaError_t prepare_raster_3(int* blocks_flat, int* blocks_vtx, int* blocks_bwd);
 cudaError_t launch_raster_3(int mode, const Ws& ws, int grid, cudaStream_t st);
 cudaError_t overflow_occupancy(int* blocks_per_sm);
@@ -125,7 +126,9 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
           prepare_raster_3(&d.blocks_flat, &d.blocks_vtx, &blocks_bwd) != cudaSuccess ||
           overflow_occupancy(&d.ovf_blocks) != cudaSuccess ||
           cudaFuncSetAttribute(k_bin_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(kSortSmemCap * sizeof(unsigned long long))) != cudaSuccess)
+                               (int)(kSortSmemCap * sizeof(unsigned long long))) != cudaSuccess ||
+          cudaFuncSetAttribute(k_bin_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kSortBigCap * sizeof(unsigned long long))) != cudaSuccess)
         return LR_ERR_CUDA;
       d.scratch = static_cast<unsigned char*>(p);
       d.blocks_flat = d.blocks_flat > 0 ? d.blocks_flat : 1;
@@ -192,6 +195,7 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
   k_bin_scan<<<1, 1024, 0, st>>>(ws);
   if (chunks > 0) k_bin_scatter<<<chunks, kBinThreads, 0, st>>>(ws);
   k_bin_sort<<<(int)nbins, 256, kSortSmemCap * sizeof(unsigned long long), st>>>(ws);
+  k_bin_sort_big<<<ds.sms, kSortBigThreads, kSortBigCap * sizeof(unsigned long long), st>>>(ws);
   const bool vtx = Q > 0 && q.color_mode == LR_COLOR_VERTEX;
   if (launch_raster_3(vtx ? 1 : 0, ws, ds.sms * (vtx ? ds.blocks_vtx : ds.blocks_flat), st) != cudaSuccess)
     return LR_ERR_CUDA;
