@@ -277,8 +277,16 @@ def run_gpu(args):
 
     scene = WORKLOADS[args.workload][1](rank)
     W, H = scene.width, scene.height
-    r = P.Renderer(sorter_k=args.k, timing=True)
     ds = P.DeviceScene.from_scene(scene, device=dev)
+    tuned = None
+    if args.k == 0:
+        # the sorter capacity K picked by the autotuner for this workload (any K gives the
+        # same exact result; it only moves pixels between the sorter and the exact path)
+        from paper_2405_13364_gb300 import autotune
+        tuned = autotune.tune(ds, W, H, ks=(1, 2, 3, 4), ctas_per_sm=(0,), reps=3, device=dev)
+        args.k = tuned["sorter_k"]
+    carry = bool(tuned and tuned.get("carry_colors"))
+    r = P.Renderer(sorter_k=args.k, timing=True, carry_colors=carry)
     out = r.make_outputs(W, H)
     view = r.view_struct(ds, W, H, out)
     # size the workspace once (retries on reference overflow), then render without checks
@@ -393,6 +401,9 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload][0], "frame": f"{W}x{H}", "quads": scene.num_quads,
                    "fragments_per_frame": frags, "sorter_k": args.k,
+                   "carry_colors": carry,
+                   "autotune_ms": None if tuned is None else
+                   {f"k{t['sorter_k']}{'c' if t['carry_colors'] else ''}": round(t["ms"], 4) for t in tuned["table"]},
                    "l2": "flushed before every step (512 MiB write, outside the timed events)",
                    "parallelism": f"replicas x{world} (one frame per GPU per step)"},
         "stage_ms": stages,
@@ -454,7 +465,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--k", type=int, default=3)
+    ap.add_argument("--k", type=int, default=0, help="sorter capacity K; 0 = autotuned")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--profile", action="store_true", help="short run for ncu (see run_profile)")

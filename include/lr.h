@@ -52,7 +52,10 @@ enum { LR_COLOR_FLAT = 0, LR_COLOR_VERTEX = 1 };
 
 /* lr_config.flags */
 enum {
-  LR_FLAG_TIMING = 1        /* record per-stage CUDA events; lr_get_stats reports stage_ms */
+  LR_FLAG_TIMING = 1,       /* record per-stage CUDA events; lr_get_stats reports stage_ms */
+  LR_FLAG_CARRY_COLORS = 2  /* flat-colour scenes too: the per-pixel sorter carries each
+                               fragment's colour (fetched once per half-block) instead of
+                               reading it when the fragment is blended (a tuning choice) */
 };
 
 /* Creation-time parameters. Zero selects the default. */

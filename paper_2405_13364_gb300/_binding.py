@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "LR_OK", 1: "LR_PENDING", -1: "LR_ERR_INVALID_ARG", -2: "LR_E
 LR_COLOR_FLAT = 0
 LR_COLOR_VERTEX = 1
 LR_FLAG_TIMING = 1
+LR_FLAG_CARRY_COLORS = 2
 
 
 class LrError(RuntimeError):

@@ -19,10 +19,13 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 OBJ_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "liblr.so")
+STAMP = os.path.join(OUT_DIR, "build_flags.txt")   # extra flags the library was built with
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xptxas", "-warn-spills", "-I", INCLUDE, "-I", CSRC]
+# extra nvcc flags (e.g. -DLR_RASTER_MIN_BLOCKS=3 for occupancy experiments)
+EXTRA = os.environ.get("LR_NVCC_FLAGS", "").split()
 
 
 def _nvcc() -> str:
@@ -42,8 +45,11 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return False
+    with open(STAMP) as f:
+        if f.read() != " ".join(EXTRA):
+            return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
@@ -58,9 +64,9 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
 
     def compile_one(src):
         obj = os.path.join(OBJ_DIR, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *EXTRA, "-c", src, "-o", obj]
         if src.endswith(".cpp"):
-            cmd = [nvcc, "-x", "cu", *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+            cmd = [nvcc, "-x", "cu", *ARCH, *NVCC_FLAGS, *EXTRA, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {os.path.basename(src)}:\n{r.stdout}\n{r.stderr}")
@@ -80,6 +86,8 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(" ".join(EXTRA))
     return LIB
 
 

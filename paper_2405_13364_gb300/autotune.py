@@ -59,8 +59,10 @@ def lookup(width, height, num_quads, color_mode, device=None):
 
 
 def tune(scene, width: int, height: int, ks=DEFAULT_KS, ctas_per_sm=(0,), reps: int = 5,
-         use_cache: bool = True, device=None):
-    """scene: a DeviceScene. Returns {'sorter_k', 'raster_ctas_per_sm', 'ms', 'table'}."""
+         use_cache: bool = True, device=None, carry=None):
+    """scene: a DeviceScene. Returns {'sorter_k', 'raster_ctas_per_sm', 'carry_colors', 'ms',
+    'table'}. carry: candidates for carrying flat colours in the sorter (default: both for
+    flat-colour scenes)."""
     from . import Renderer
     key = workload_key(width, height, scene.num_quads, scene.color_mode, device)
     cache = _load_cache() if use_cache else {}
@@ -68,9 +70,12 @@ def tune(scene, width: int, height: int, ks=DEFAULT_KS, ctas_per_sm=(0,), reps: 
         return cache[key]
     table = []
     ref_img = None
-    for k in ks:
-        for c in ctas_per_sm:
-            r = Renderer(sorter_k=k, raster_ctas_per_sm=c, device=device)
+    if carry is None:
+        carry = (False, True) if scene.color_mode == 0 else (False,)
+    cands = [(k, c, cc) for k in ks for c in ctas_per_sm for cc in carry]
+    for k, c, cc in cands:
+        if True:
+            r = Renderer(sorter_k=k, raster_ctas_per_sm=c, device=device, carry_colors=cc)
             out = r.make_outputs(width, height)
             view = r.view_struct(scene, width, height, out)
             st = r.render_views([view])                    # sizes the workspace, checked
@@ -88,12 +93,12 @@ def tune(scene, width: int, height: int, ks=DEFAULT_KS, ctas_per_sm=(0,), reps: 
                 torch.cuda.synchronize()
                 times.append(a.elapsed_time(b))
             ovf = B_overflow(r)
-            table.append(dict(sorter_k=k, raster_ctas_per_sm=c, ms=statistics.median(times),
+            table.append(dict(sorter_k=k, raster_ctas_per_sm=c, carry_colors=cc, ms=statistics.median(times),
                               overflow_pixels=ovf, fragments=int(st.fragments)))
             r.close()
     best = min(table, key=lambda t: t["ms"])
     result = dict(sorter_k=best["sorter_k"], raster_ctas_per_sm=best["raster_ctas_per_sm"],
-                  ms=best["ms"], table=table)
+                  carry_colors=best["carry_colors"], ms=best["ms"], table=table)
     if use_cache:
         cache[key] = result
         _save_cache(cache)

@@ -476,8 +476,9 @@ static lr_status launch_sequence(lr_ctx* ctx, const Prepared& P, cudaStream_t st
   k_bin_sort<<<L.total_bins, 256, kSortSmemCap * sizeof(unsigned long long), st>>>(ws);
   k_bin_sort_big<<<ctx->sms, kSortBigThreads, kSortBigCap * sizeof(unsigned long long), st>>>(ws);
   rec(ctx, timed, 5, st);
-  const int mode = bwd ? 2 : (P.any_vertex ? 1 : 0);
-  const int rblocks = bwd ? ctx->raster_blocks_bwd : (P.any_vertex ? ctx->raster_blocks_vtx : ctx->raster_blocks_flat);
+  const bool carry = P.any_vertex || (ctx->cfg.flags & LR_FLAG_CARRY_COLORS);
+  const int mode = bwd ? 2 : (carry ? 1 : 0);
+  const int rblocks = bwd ? ctx->raster_blocks_bwd : (carry ? ctx->raster_blocks_vtx : ctx->raster_blocks_flat);
   cudaError_t e = ctx->variant->launch(mode, ws, ctx->sms * rblocks, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "raster launch");
   rec(ctx, timed, 6, st);

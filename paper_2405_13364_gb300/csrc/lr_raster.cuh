@@ -34,6 +34,12 @@ namespace lr {
 constexpr uint32_t kTriValid = 1u, kTriFast = 2u, kTriFlatCol = 4u;   // + corr bits 3..5
 constexpr unsigned long long kSent = ~0ull;
 constexpr int kRasterThreads = 256;
+#ifndef LR_RASTER_MIN_BLOCKS
+// resident CTAs per SM requested from the compiler: 3 caps registers at 80 per thread (24
+// warps per SM, a few spills), measured faster than 2 (128 registers) on both the layer
+// and the particle workloads; without a bound the compiler takes ~160 and one CTA fits
+#define LR_RASTER_MIN_BLOCKS 3
+#endif
 constexpr int kRasterWarps = kRasterThreads / 32;
 constexpr int kOvfKeep = 480;               // fragments composited per overflow pass
 constexpr int kOvfBuf = 1024;               // per-warp overflow buffer (power of two)
@@ -162,19 +168,16 @@ __device__ __forceinline__ uint32_t row_cover(int r, int sx) {
 __device__ __forceinline__ uint32_t tri_mask_fast(const int e[3], const int sx[3], const int sy[3],
                                                   const int box[4]) {
   uint32_t mask = 0;
+  const uint32_t cols = ((2u << box[1]) - 1u) & ~((1u << box[0]) - 1u);
 #pragma unroll 1
-  for (int ly = 0; ly < kHbH; ++ly) {
-    uint32_t row = 0xFFu;
+  for (int ly = box[2]; ly <= box[3]; ++ly) {
+    uint32_t row = cols;
 #pragma unroll
     for (int k = 0; k < 3; ++k)
       row &= row_cover((int)((uint32_t)e[k] + (uint32_t)ly * (uint32_t)sy[k]), sx[k]);
     mask |= row << (ly * kHbW);
   }
-  const uint32_t cols = ((2u << box[1]) - 1u) & ~((1u << box[0]) - 1u);
-  uint32_t rows = 0;
-#pragma unroll
-  for (int ly = 0; ly < kHbH; ++ly) rows |= (ly >= box[2] && ly <= box[3]) ? (cols << (ly * kHbW)) : 0u;
-  return mask & rows;
+  return mask;
 }
 
 // The same with exact 64-bit edge values, pixel by pixel (large triangles).
@@ -302,7 +305,7 @@ __device__ __forceinline__ void write_pixel(const ViewDev& V, long long pidx, fl
 }
 
 template <int K, bool VTX, bool BWD>
-__global__ __launch_bounds__(kRasterThreads) void k_raster(Ws ws) {
+__global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster(Ws ws) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lx = lane & (kHbW - 1), ly = lane >> 3;

@@ -15,7 +15,7 @@ def test_autotune_small(tmp_path, monkeypatch):
     ds = P.DeviceScene.from_scene(s)
     res = autotune.tune(ds, s.width, s.height, ks=(1, 2, 3, 8), ctas_per_sm=(0, 1), reps=2)
     assert res["sorter_k"] in (1, 2, 3, 8)
-    assert len(res["table"]) == 8
+    assert len(res["table"]) == 8      # per-vertex colours: no colour-carrying variant
     # K = 1 cannot order interpenetrating layers by itself: more exact-path pixels
     by_k = {t["sorter_k"]: t["overflow_pixels"] for t in res["table"] if t["raster_ctas_per_sm"] == 0}
     assert by_k[1] >= by_k[8]
