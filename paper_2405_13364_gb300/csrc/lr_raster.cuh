@@ -45,14 +45,16 @@ constexpr int kOvfKeep = 480;               // fragments composited per overflow
 constexpr int kOvfBuf = 1024;               // per-warp overflow buffer (power of two)
 constexpr int kOvfThreads = 128;
 
-struct TriSm {
-  int e[3];        // biased edge value (E + owned - 1) at the half-block's first pixel centre
-  int sx[3];       // change per pixel step in x
-  int sy[3];       // change per pixel step in y
-  float q0, d1, d2, inv;   // 1/w at v0, (q1 - q0), (q2 - q0), 1 / (float)area
-  uint32_t id;     // 2 * quad (view-local) + triangle
-  uint32_t flags;  // kTri* | (1 - owned_e) << (3 + e)
+// Per (triangle, half-block) record read by the fragment loop, laid out for three 16-byte
+// shared-memory loads. Edges 1 (v2->v0) and 2 (v0->v1) give the barycentric numerators
+// of the depth key; edge 0 is only needed for coverage, which the masks already hold.
+struct __align__(16) TriSm {
+  int4 ea;         // e1, e2: biased edge values (E + owned - 1) at the half-block's first
+                   // pixel centre; sx1, sx2: change per pixel step in x
+  int4 eb;         // sy1, sy2: change per pixel step in y; flags; id (2 * quad + triangle)
+  float4 kq;       // q0 = 1/w at v0, d1 = q1 - q0, d2 = q2 - q0, inv = 1 / (float)area
   int X[3], Y[3];  // vertices after the orientation fix (64-bit path)
+  int pad[2];
 };
 
 // dynamic shared memory of k_raster: per warp 64 triangle records, a 64-entry candidate
@@ -105,11 +107,7 @@ __device__ __forceinline__ bool setup_tri(TriSm& T, const int X[4], const int Y[
   cor[0] = 0; cor[1] = ib; cor[2] = ic;
   T.X[0] = xa; T.X[1] = xb; T.X[2] = xc;
   T.Y[0] = ya; T.Y[1] = yb; T.Y[2] = yc;
-  T.q0 = qa;
-  T.d1 = __fsub_rn(qb, qa);
-  T.d2 = __fsub_rn(qc, qa);
-  T.inv = __fdiv_rn(1.0f, __ll2float_rn(A));
-  T.id = 2u * jl + (uint32_t)t;
+  T.kq = make_float4(qa, __fsub_rn(qb, qa), __fsub_rn(qc, qa), __fdiv_rn(1.0f, __ll2float_rn(A)));
   uint32_t flags = kTriValid;
   bool fast = true;
   const long long P0x = 256LL * ox + 128, P0y = 256LL * oy + 128;
@@ -124,13 +122,14 @@ __device__ __forceinline__ bool setup_tri(TriSm& T, const int X[4], const int Y[
     const long long sx = -256 * dy, sy = 256 * dx;
     const long long c1 = e0 + (kHbW - 1) * sx, c2 = e0 + (kHbH - 1) * sy, c3 = c1 + (kHbH - 1) * sy;
     fast &= (e0 > -lim && e0 < lim && c1 > -lim && c1 < lim && c2 > -lim && c2 < lim && c3 > -lim && c3 < lim);
-    T.e[k] = le[k] = (int)e0;
-    T.sx[k] = lsx[k] = (int)sx;
-    T.sy[k] = lsy[k] = (int)sy;
+    le[k] = (int)e0;
+    lsx[k] = (int)sx;
+    lsy[k] = (int)sy;
     if (!owned) flags |= 1u << (3 + k);
   }
   if (fast) flags |= kTriFast;
-  T.flags = flags;
+  T.ea = make_int4(le[1], le[2], lsx[1], lsx[2]);
+  T.eb = make_int4(lsy[1], lsy[2], (int)flags, (int)(2u * jl + (uint32_t)t));
   return true;
 }
 
@@ -190,7 +189,7 @@ static __device__ __noinline__ uint32_t tri_mask_slow(const TriSm& T, int ox, in
       bool cov = true;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const bool owned = !(T.flags & (1u << (3 + k)));
+        const bool owned = !((uint32_t)T.eb.z & (1u << (3 + k)));
         cov &= e[k] > 0 || (e[k] == 0 && owned);
       }
       if (cov) mask |= 1u << (ly * kHbW + lx);
@@ -364,17 +363,15 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
         for (int t = 0; t < 2; ++t) {
           TriSm& T = tris[2 * lane + t];
           int cor[3], box[4], le[3], lsx[3], lsy[3];
-          if (!setup_tri(T, X, Y, qv, info, t, jl, ox, oy, cor, box, le, lsx, lsy)) {
-            T.flags = 0;
-            continue;
-          }
-          const uint32_t mk = (T.flags & kTriFast) ? tri_mask_fast(le, lsx, lsy, box) : tri_mask_slow(T, ox, oy, box);
+          if (!setup_tri(T, X, Y, qv, info, t, jl, ox, oy, cor, box, le, lsx, lsy)) continue;
+          const uint32_t mk = ((uint32_t)T.eb.z & kTriFast) ? tri_mask_fast(le, lsx, lsy, box)
+                                                            : tri_mask_slow(T, ox, oy, box);
           if (t == 0) tm0 = mk; else tm1 = mk;
           if (VTX) {
             float4* qc = qcs + (2 * lane + t) * 3;
             if (!vtx_view) {
               qc[0] = __ldg(reinterpret_cast<const float4*>(V.col) + jl);
-              T.flags |= kTriFlatCol;
+              T.eb.z |= (int)kTriFlatCol;
             } else {
               uint4 vi;
               if (V.idx) vi = __ldg(reinterpret_cast<const uint4*>(V.idx) + jl);
@@ -400,16 +397,19 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
       while (bits) {
         const int c = __ffs(bits) - 1;
         bits &= bits - 1;
-#pragma unroll 1
-        for (int t = 0; t < 2; ++t) {
-          if (!(((t ? m1 : m0) >> c) & 1u)) continue;
+        // T0 first; T1 as well when both triangles of the quad cover the pixel
+        int t = ((m0 >> c) & 1u) ? 0 : 1;
+        const int last_t = ((m1 >> c) & 1u) ? 1 : 0;
+        for (; t <= last_t; ++t) {
           const TriSm& T = tris[2 * c + t];
-          const uint32_t fl = T.flags;
+          const int4 ea = T.ea, eb = T.eb;
+          const float4 kq = T.kq;
+          const uint32_t fl = (uint32_t)eb.z, id = (uint32_t)eb.w;
           float f1, f2;
           if (fl & kTriFast) {
-            const int e1 = (int)((uint32_t)T.e[1] + (uint32_t)lx * (uint32_t)T.sx[1] + (uint32_t)ly * (uint32_t)T.sy[1] +
+            const int e1 = (int)((uint32_t)ea.x + (uint32_t)lx * (uint32_t)ea.z + (uint32_t)ly * (uint32_t)eb.x +
                                  ((fl >> 4) & 1u));
-            const int e2 = (int)((uint32_t)T.e[2] + (uint32_t)lx * (uint32_t)T.sx[2] + (uint32_t)ly * (uint32_t)T.sy[2] +
+            const int e2 = (int)((uint32_t)ea.y + (uint32_t)lx * (uint32_t)ea.w + (uint32_t)ly * (uint32_t)eb.y +
                                  ((fl >> 5) & 1u));
             f1 = __int2float_rn(e1);
             f2 = __int2float_rn(e2);
@@ -419,12 +419,12 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
             f1 = __ll2float_rn(e[1]);
             f2 = __ll2float_rn(e[2]);
           }
-          const float l1 = __fmul_rn(f1, T.inv);
-          const float l2 = __fmul_rn(f2, T.inv);
-          const float key = __fadd_rn(T.q0, __fadd_rn(__fmul_rn(l1, T.d1), __fmul_rn(l2, T.d2)));
-          const unsigned long long sk = ((unsigned long long)__float_as_uint(key) << 32) | T.id;
+          const float l1 = __fmul_rn(f1, kq.w);
+          const float l2 = __fmul_rn(f2, kq.w);
+          const float key = __fadd_rn(kq.x, __fadd_rn(__fmul_rn(l1, kq.y), __fmul_rn(l2, kq.z)));
+          const unsigned long long sk = ((unsigned long long)__float_as_uint(key) << 32) | id;
           ++cnt;
-          if (V.hash) hsh += splitmix64(T.id);
+          if (V.hash) hsh += splitmix64(id);
           if (st.flagged) continue;
           float4 col = make_float4(0.f, 0.f, 0.f, 0.f);
           if (VTX) {
