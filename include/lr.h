@@ -134,7 +134,8 @@ typedef struct {
  *   rec_rect  u32[Q][2]  pixel-centre AABB: px0 | px1 << 16, py0 | py1 << 16
  *                        (0x0000FFFF, 0x0000FFFF for a culled quad)
  *   rec_info  u32[Q]     bit 0/1: triangle 0/1 has non-zero area, bit 2: spans more than
- *                        2x2 bins, bits 8..11: cull reason (0 = visible)
+ *                        4x4 bins, bit 3: all vertices at the same 1/w, bits 8..11: cull
+ *                        reason (0 = visible)
  *   bin_off   u32[bins+1] start of each bin's reference list in refs
  *   refs      u64[capacity] per-bin reference lists, sorted front to back
  * Quads, bins and pixels of a batch are numbered view after view. */

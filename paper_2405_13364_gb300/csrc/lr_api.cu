@@ -74,7 +74,7 @@ static const RasterVariant kVariants[] = {
 };
 
 struct Layout {
-  size_t ctrl, views, rec_xy, rec_q, rec_rect, rec_info, bin_count, bin_off, bin_cursor, bin_order;
+  size_t ctrl, views, rec_xy, rec_q, rec_rect, rec_info, rec_rep, bin_count, bin_off, bin_cursor, bin_order;
   size_t refs, refs_tmp, ref_hb, ovf_list, total;
   long long total_quads = 0, total_pix = 0, refs_cap = 0;
   int total_bins = 0, total_chunks = 0;
@@ -102,6 +102,7 @@ static Layout make_layout(int n, const long long* Q, const int* W, const int* H)
   L.rec_q = take(sizeof(float4) * (size_t)L.total_quads);
   L.rec_rect = take(sizeof(uint2) * (size_t)L.total_quads);
   L.rec_info = take(sizeof(uint32_t) * (size_t)L.total_quads);
+  L.rec_rep = take(sizeof(float) * (size_t)L.total_quads);
   L.bin_count = take(sizeof(uint32_t) * (size_t)L.total_bins);
   L.bin_off = take(sizeof(uint32_t) * ((size_t)L.total_bins + 1));
   L.bin_cursor = take(sizeof(uint32_t) * (size_t)L.total_bins);
@@ -151,6 +152,7 @@ static Ws make_ws(const Layout& L, void* base, int n_views) {
   w.rec_q = reinterpret_cast<float4*>(b + L.rec_q);
   w.rec_rect = reinterpret_cast<uint2*>(b + L.rec_rect);
   w.rec_info = reinterpret_cast<uint32_t*>(b + L.rec_info);
+  w.rec_rep = reinterpret_cast<float*>(b + L.rec_rep);
   w.bin_count = reinterpret_cast<uint32_t*>(b + L.bin_count);
   w.bin_off = reinterpret_cast<uint32_t*>(b + L.bin_off);
   w.bin_cursor = reinterpret_cast<uint32_t*>(b + L.bin_cursor);
@@ -233,7 +235,7 @@ extern "C" lr_status lr_create(const lr_config* config, lr_ctx** out_ctx) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bin_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)(kSortSmemCap * sizeof(unsigned long long)));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bin_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)(kSortBigCap * sizeof(unsigned long long)));
+                                                 (int)(2 * kSortBigCap * sizeof(unsigned long long)));
   if (e == cudaSuccess) e = overflow_occupancy(&c->ovf_blocks);
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&c->host_ctrl), sizeof(Ctrl));
   for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev[i]);
@@ -474,7 +476,7 @@ static lr_status launch_sequence(lr_ctx* ctx, const Prepared& P, cudaStream_t st
   if (L.total_chunks > 0) k_bin_scatter<<<L.total_chunks, kBinThreads, 0, st>>>(ws);
   rec(ctx, timed, 4, st);
   k_bin_sort<<<L.total_bins, 256, kSortSmemCap * sizeof(unsigned long long), st>>>(ws);
-  k_bin_sort_big<<<ctx->sms, kSortBigThreads, kSortBigCap * sizeof(unsigned long long), st>>>(ws);
+  k_bin_sort_big<<<ctx->sms, kSortBigThreads, 2 * kSortBigCap * sizeof(unsigned long long), st>>>(ws);
   rec(ctx, timed, 5, st);
   const bool carry = P.any_vertex || (ctx->cfg.flags & LR_FLAG_CARRY_COLORS);
   const int mode = bwd ? 2 : (carry ? 1 : 0);

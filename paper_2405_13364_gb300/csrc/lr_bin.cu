@@ -18,12 +18,13 @@
 //   k_bin_sort     Stage-1 depth sort: sorts each bin's references ascending, i.e. front
 //                  to back by a representative depth, ties with the higher quad index
 //                  first. Bins with fewer than 4096 references: one 256-thread CTA per
-//                  bin, bitonic sort in shared memory.
+//                  bin, a bitonic network on keys held in registers (exchanges through
+//                  registers, warp shuffles, or shared memory across warps).
 //   k_bin_sort_big The high-density bins (4096 references or more; the paper's "high"
 //                  category): persistent 1024-thread CTAs take them from the front
-//                  of the size-ordered bin list and sort up to 16384 references in shared
-//                  memory; beyond that, 16384-reference runs are merged through a global
-//                  buffer.
+//                  of the size-ordered bin list and merge-sort runs of up to 8192
+//                  references in shared memory; longer lists merge their runs through a
+//                  global buffer.
 #include "lr_common.cuh"
 
 namespace lr {
@@ -71,28 +72,14 @@ __device__ __forceinline__ bool quad_may_touch_bin(const Ws& ws, long long q, ui
          ((info & kInfoTri1) && tri_may_touch_bin(X, Y, 1, bx, by, W, H));
 }
 
-// Representative depth of a quad inside a bin: the plane of one triangle evaluated (in
-// plain fp32, approximately) at the centre of the quad's pixel AABB clipped to the bin,
-// clamped to the range of the quad's vertex 1/w. Only the order quality of stage 1
-// depends on it; exactness is restored by the per-pixel sorter and the overflow path.
+// Per-bin representative depth of a quad that spans several bins.
 __device__ __forceinline__ float rep_depth(const Ws& ws, long long q, uint32_t info, int x0, int x1,
                                            int y0, int y1) {
   const int4 a = ws.rec_xy[2 * q], b = ws.rec_xy[2 * q + 1];
   const float4 qq = ws.rec_q[q];
-  const float Xs[4] = {(float)a.x, (float)a.z, (float)b.x, (float)b.z};
-  const float Ys[4] = {(float)a.y, (float)a.w, (float)b.y, (float)b.w};
+  const int X[4] = {a.x, a.z, b.x, b.z}, Y[4] = {a.y, a.w, b.y, b.w};
   const float Q[4] = {qq.x, qq.y, qq.z, qq.w};
-  const float qmin = fminf(fminf(Q[0], Q[1]), fminf(Q[2], Q[3]));
-  const float qmax = fmaxf(fmaxf(Q[0], Q[1]), fmaxf(Q[2], Q[3]));
-  const int i1 = (info & kInfoTri0) ? 1 : 2, i2 = (info & kInfoTri0) ? 2 : 3;
-  const float px = 128.0f * (float)(x0 + x1) + 128.0f, py = 128.0f * (float)(y0 + y1) + 128.0f;
-  const float A = (Xs[i1] - Xs[0]) * (Ys[i2] - Ys[0]) - (Ys[i1] - Ys[0]) * (Xs[i2] - Xs[0]);
-  if (!(fabsf(A) > 0.0f)) return qmax;
-  const float l1 = ((Xs[0] - Xs[i2]) * (py - Ys[i2]) - (Ys[0] - Ys[i2]) * (px - Xs[i2])) / A;
-  const float l2 = ((Xs[i1] - Xs[0]) * (py - Ys[0]) - (Ys[i1] - Ys[0]) * (px - Xs[0])) / A;
-  float r = Q[0] + l1 * (Q[i1] - Q[0]) + l2 * (Q[i2] - Q[0]);
-  r = fminf(fmaxf(r, qmin), qmax);
-  return r > 0.0f ? r : qmin;
+  return rep_depth_of(X, Y, Q, info, x0, x1, y0, y1);
 }
 
 __device__ __forceinline__ unsigned long long ref_key(float rep, long long q) {
@@ -264,27 +251,15 @@ __global__ __launch_bounds__(kBinThreads) void k_bin_scatter(Ws ws) {
     const int x1 = min((int)(rect.x >> 16), (bx << kBinLog2) + kBin - 1);
     const int y0 = max((int)(rect.y & 0xffff), by << kBinLog2);
     const int y1 = min((int)(rect.y >> 16), (by << kBinLog2) + kBin - 1);
-    if (slot < (uint32_t)ws.refs_cap) ws.refs[slot] = ref_key(rep_depth(ws, q, info, x0, x1, y0, y1), q);
+    // a quad inside one bin, or of constant depth: its per-quad value; else the plane at its
+    // box clipped to this bin
+    const bool one_bin = ((rect.x & 0xffff) >> kBinLog2) == ((rect.x >> 16) >> kBinLog2) &&
+                         ((rect.y & 0xffff) >> kBinLog2) == ((rect.y >> 16) >> kBinLog2);
+    const float rep = (one_bin || (info & kInfoFlatDepth)) ? ws.rec_rep[q] : rep_depth(ws, q, info, x0, x1, y0, y1);
+    if (slot < (uint32_t)ws.refs_cap) ws.refs[slot] = ref_key(rep, q);
   });
 }
 
-// ---- per-bin sort --------------------------------------------------------------------
-
-__device__ void smem_bitonic_sort(unsigned long long* s, int n2) {
-  // ascending bitonic sort of s[0, n2), n2 a power of two, by the whole CTA
-  for (int k = 2; k <= n2; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < (n2 >> 1); i += blockDim.x) {
-        const int lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
-        const int hi = lo | j;
-        const bool up = (lo & k) == 0;
-        const unsigned long long a = s[lo], b = s[hi];
-        if ((a > b) == up) { s[lo] = b; s[hi] = a; }
-      }
-      __syncthreads();
-    }
-  }
-}
 
 // Merge sorted runs a[0, na) and b[0, nb) into out, split evenly over the CTA (merge path).
 __device__ void cta_merge(const unsigned long long* a, int na, const unsigned long long* b, int nb,
@@ -331,6 +306,84 @@ __device__ void write_hb_masks(const Ws& ws, const unsigned long long* r, uint32
   }
 }
 
+// one bitonic step between keys of the same thread (J < E; compile-time register indices)
+template <int E, int J>
+__device__ __forceinline__ void thread_step(unsigned long long (&v)[E], int t, int k) {
+  if (J >= E) return;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    if (e & J) continue;
+    const int i = E * t + e;
+    const unsigned long long a = v[e], b = v[(e | J) < E ? (e | J) : e];
+    const bool up = (i & k) == 0;
+    const bool sw = up ? (a > b) : (a < b);
+    v[e] = sw ? b : a;
+    v[(e | J) < E ? (e | J) : e] = sw ? a : b;
+  }
+}
+
+// Ascending sort of g[0, n) (n <= E * blockDim.x) by the whole CTA, E keys per thread in
+// registers (element i = E * thread + e; missing elements padded with ~0). Bitonic network:
+// exchanges with a partner in the same thread use registers, in the same warp shuffles,
+// in another warp one round trip through shared memory (sbuf, E * blockDim.x keys).
+template <int E>
+__device__ void cta_sort_regs(unsigned long long* g, int n, unsigned long long* sbuf) {
+  const int t = threadIdx.x;
+  const int N = E * (int)blockDim.x;
+  unsigned long long v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = E * t + e;
+    v[e] = i < n ? g[i] : ~0ull;
+  }
+  for (int k = 2; k <= N; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32 * E) {                       // partner in another warp
+#pragma unroll
+        for (int e = 0; e < E; ++e) sbuf[E * t + e] = v[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = E * t + e;
+          const unsigned long long w = sbuf[i ^ j];
+          const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
+          v[e] = keep_min ? (v[e] < w ? v[e] : w) : (v[e] > w ? v[e] : w);
+        }
+        __syncthreads();
+      } else if (j >= E) {                     // partner in the same warp
+        const int d = j / E;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = E * t + e;
+          const unsigned long long w = __shfl_xor_sync(0xffffffffu, v[e], d);
+          const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
+          v[e] = keep_min ? (v[e] < w ? v[e] : w) : (v[e] > w ? v[e] : w);
+        }
+      } else {                                 // partner in the same thread
+        if (j == 8) thread_step<E, 8>(v, t, k);
+        else if (j == 4) thread_step<E, 4>(v, t, k);
+        else if (j == 2) thread_step<E, 2>(v, t, k);
+        else thread_step<E, 1>(v, t, k);
+      }
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = E * t + e;
+    if (i < n) g[i] = v[e];
+  }
+}
+
+// dispatch on the number of keys per thread (powers of two up to 16)
+__device__ void cta_sort(unsigned long long* g, int n, unsigned long long* sbuf) {
+  const int per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
+  if (per <= 1) cta_sort_regs<1>(g, n, sbuf);
+  else if (per <= 2) cta_sort_regs<2>(g, n, sbuf);
+  else if (per <= 4) cta_sort_regs<4>(g, n, sbuf);
+  else if (per <= 8) cta_sort_regs<8>(g, n, sbuf);
+  else cta_sort_regs<16>(g, n, sbuf);
+}
+
 __global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {
   extern __shared__ unsigned long long sbuf[];
   if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
@@ -340,15 +393,59 @@ __global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {
   if (n >= kSortSmemCap) return;   // high-density: k_bin_sort_big
   unsigned long long* r = ws.refs + off;
   if (n > 1) {
-    int n2 = 32;
-    while (n2 < n) n2 <<= 1;
-    for (int i = threadIdx.x; i < n2; i += blockDim.x) sbuf[i] = i < n ? r[i] : ~0ull;
-    __syncthreads();
-    smem_bitonic_sort(sbuf, n2);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = sbuf[i];
+    cta_sort(r, n, sbuf);
     __syncthreads();
   }
   write_hb_masks(ws, r, ws.ref_hb + off, n, bin);
+}
+
+// Ascending merge sort of g[0, n) (n <= kSortBigCap) in shared memory by the whole CTA:
+// 32-key runs sorted by warp shuffles, then merge levels between two shared buffers, each
+// thread producing an equal slice of every level's output (merge path search + a
+// sequential merge of its slice).
+__device__ void cta_merge_sort_smem(unsigned long long* g, int n, unsigned long long* A,
+                                    unsigned long long* Bf) {
+  int N = 32;
+  while (N < n) N <<= 1;
+  const int T = (int)blockDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = T >> 5;
+  for (int i = t; i < N; i += T) A[i] = i < n ? g[i] : ~0ull;
+  __syncthreads();
+  for (int r = warp; r < N / 32; r += nw) {
+    unsigned long long v = A[32 * r + lane];
+    for (int k = 2; k <= 32; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, j);
+        const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+        v = keep_min ? (v < w ? v : w) : (v > w ? v : w);
+      }
+    A[32 * r + lane] = v;
+  }
+  __syncthreads();
+  unsigned long long* src = A;
+  unsigned long long* dst = Bf;
+  for (int w = 32; w < N; w <<= 1) {
+    const int P = N / T > 0 ? N / T : 1;      // outputs per thread; divides 2w
+    for (int d0 = t * P; d0 < N; d0 += T * P) {
+      const int base = (d0 / (2 * w)) * (2 * w), loc = d0 - base;
+      const unsigned long long* a = src + base;
+      const unsigned long long* b = src + base + w;
+      int lo = max(0, loc - w), hi = min(loc, w);
+      while (lo < hi) {
+        const int i = (lo + hi) >> 1;
+        if (a[i] < b[loc - i - 1]) lo = i + 1; else hi = i;
+      }
+      int i = lo, j = loc - lo;
+      for (int d = 0; d < P; ++d) {
+        const bool ta = j >= w || (i < w && a[i] < b[j]);
+        dst[base + loc + d] = ta ? a[i] : b[j];
+        i += ta;
+        j += !ta;
+      }
+    }
+    __syncthreads();
+    unsigned long long* tmp = src; src = dst; dst = tmp;
+  }
+  for (int i = t; i < n; i += T) g[i] = src[i];
 }
 
 __global__ __launch_bounds__(kSortBigThreads) void k_bin_sort_big(Ws ws) {
@@ -371,13 +468,7 @@ __global__ __launch_bounds__(kSortBigThreads) void k_bin_sort_big(Ws ws) {
     const int run0 = n <= kSortBigCap ? n : kSortBigCap;
     // sort runs of up to kSortBigCap references in shared memory
     for (int s = 0; s < n; s += run0) {
-      const int m = min(run0, n - s);
-      int n2 = 32;
-      while (n2 < m) n2 <<= 1;
-      for (int i = threadIdx.x; i < n2; i += blockDim.x) sbuf[i] = i < m ? r[s + i] : ~0ull;
-      __syncthreads();
-      smem_bitonic_sort(sbuf, n2);
-      for (int i = threadIdx.x; i < m; i += blockDim.x) r[s + i] = sbuf[i];
+      cta_merge_sort_smem(r + s, min(run0, n - s), sbuf, sbuf + kSortBigCap);
       __syncthreads();
     }
     // merge the runs through the global buffer (only for more than kSortBigCap)

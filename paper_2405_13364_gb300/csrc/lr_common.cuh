@@ -19,7 +19,7 @@ constexpr int kHbW = 8, kHbH = 4;           // 8x4 half-blocks (Sec. 2, Stage 3)
 constexpr int kHbPerBin = (kBin / kHbW) * (kBin / kHbH);   // 32
 constexpr float kGuardPx = 16384.0f;        // guard band, pixels
 constexpr int kSortSmemCap = 4096;          // bins below this many refs: k_bin_sort (256 threads)
-constexpr int kSortBigCap = 16384;          // k_bin_sort_big sorts up to this many in shared memory
+constexpr int kSortBigCap = 8192;           // k_bin_sort_big sorts runs of up to this many refs
 constexpr int kSortBigThreads = 1024;
 constexpr int kHistSmemBins = 5120;         // shared-memory bin counters per CTA (Sec. 2 Stage 2)
 constexpr int kChunkQuads = 1024;           // quads per binning CTA
@@ -36,6 +36,7 @@ enum Cull : uint32_t {
 constexpr uint32_t kInfoTri0 = 1u;          // triangle 0 has non-zero area
 constexpr uint32_t kInfoTri1 = 2u;          // triangle 1 has non-zero area
 constexpr uint32_t kInfoLarge = 4u;         // bin rectangle larger than kSmallBins^2 bins
+constexpr uint32_t kInfoFlatDepth = 8u;     // all four vertices have the same 1/w
 constexpr uint32_t kRectInvisible = 0x0000FFFFu;   // rect.x value of a culled quad
 
 struct ViewDev {
@@ -93,6 +94,7 @@ struct Ws {
   float4* rec_q;             // [total_quads]: 1/w per vertex
   uint2* rec_rect;           // [total_quads]: pixel AABB (px0 | px1 << 16, py0 | py1 << 16)
   uint32_t* rec_info;        // [total_quads]: kInfo* bits | cull reason << 8
+  float* rec_rep;            // [total_quads]: representative 1/w over the quad's whole box
   uint32_t* bin_count;       // [total_bins]
   uint32_t* bin_off;         // [total_bins + 1]
   uint32_t* bin_cursor;      // [total_bins]
@@ -157,6 +159,27 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
+}
+
+// Representative depth of a quad over a pixel box: the plane of one triangle evaluated (in
+// plain fp32, approximately) at the box centre, clamped to the range of the quad's vertex
+// 1/w. Only the order quality of stage 1 (the per-bin depth sort) depends on it; exactness
+// is restored by the per-pixel sorter and the overflow path.
+__device__ __forceinline__ float rep_depth_of(const int X[4], const int Y[4], const float Q[4], uint32_t info,
+                                              int x0, int x1, int y0, int y1) {
+  const float Xs[4] = {(float)X[0], (float)X[1], (float)X[2], (float)X[3]};
+  const float Ys[4] = {(float)Y[0], (float)Y[1], (float)Y[2], (float)Y[3]};
+  const float qmin = fminf(fminf(Q[0], Q[1]), fminf(Q[2], Q[3]));
+  const float qmax = fmaxf(fmaxf(Q[0], Q[1]), fmaxf(Q[2], Q[3]));
+  const int i1 = (info & kInfoTri0) ? 1 : 2, i2 = (info & kInfoTri0) ? 2 : 3;
+  const float px = 128.0f * (float)(x0 + x1) + 128.0f, py = 128.0f * (float)(y0 + y1) + 128.0f;
+  const float A = (Xs[i1] - Xs[0]) * (Ys[i2] - Ys[0]) - (Ys[i1] - Ys[0]) * (Xs[i2] - Xs[0]);
+  if (!(fabsf(A) > 0.0f)) return qmax;
+  const float l1 = ((Xs[0] - Xs[i2]) * (py - Ys[i2]) - (Ys[0] - Ys[i2]) * (px - Xs[i2])) / A;
+  const float l2 = ((Xs[i1] - Xs[0]) * (py - Ys[0]) - (Ys[i1] - Ys[0]) * (px - Xs[0])) / A;
+  float r = Q[0] + l1 * (Q[i1] - Q[0]) + l2 * (Q[i2] - Q[0]);
+  r = fminf(fmaxf(r, qmin), qmax);
+  return r > 0.0f ? r : qmin;
 }
 
 }  // namespace lr

@@ -97,6 +97,7 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
   const size_t o_q = o; o = up256(o + 16 * (size_t)Q);
   const size_t o_rect = o; o = up256(o + 8 * (size_t)Q);
   const size_t o_info = o; o = up256(o + 4 * (size_t)Q);
+  const size_t o_rep = o; o = up256(o + 4 * (size_t)Q);
   const size_t o_cnt = o; o = up256(o + 4 * (size_t)nbins);
   const size_t o_off = o; o = up256(o + 4 * ((size_t)nbins + 1));
   const size_t o_cur = o; o = up256(o + 4 * (size_t)nbins);
@@ -128,7 +129,7 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
           cudaFuncSetAttribute(k_bin_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(kSortSmemCap * sizeof(unsigned long long))) != cudaSuccess ||
           cudaFuncSetAttribute(k_bin_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(kSortBigCap * sizeof(unsigned long long))) != cudaSuccess)
+                               (int)(2 * kSortBigCap * sizeof(unsigned long long))) != cudaSuccess)
         return LR_ERR_CUDA;
       d.scratch = static_cast<unsigned char*>(p);
       d.blocks_flat = d.blocks_flat > 0 ? d.blocks_flat : 1;
@@ -176,6 +177,7 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
   ws.rec_q = reinterpret_cast<float4*>(base + o_q);
   ws.rec_rect = reinterpret_cast<uint2*>(base + o_rect);
   ws.rec_info = reinterpret_cast<uint32_t*>(base + o_info);
+  ws.rec_rep = reinterpret_cast<float*>(base + o_rep);
   ws.bin_count = reinterpret_cast<uint32_t*>(base + o_cnt);
   ws.bin_off = reinterpret_cast<uint32_t*>(base + o_off);
   ws.bin_cursor = reinterpret_cast<uint32_t*>(base + o_cur);
@@ -195,7 +197,7 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
   k_bin_scan<<<1, 1024, 0, st>>>(ws);
   if (chunks > 0) k_bin_scatter<<<chunks, kBinThreads, 0, st>>>(ws);
   k_bin_sort<<<(int)nbins, 256, kSortSmemCap * sizeof(unsigned long long), st>>>(ws);
-  k_bin_sort_big<<<ds.sms, kSortBigThreads, kSortBigCap * sizeof(unsigned long long), st>>>(ws);
+  k_bin_sort_big<<<ds.sms, kSortBigThreads, 2 * kSortBigCap * sizeof(unsigned long long), st>>>(ws);
   const bool vtx = Q > 0 && q.color_mode == LR_COLOR_VERTEX;
   if (launch_raster_3(vtx ? 1 : 0, ws, ds.sms * (vtx ? ds.blocks_vtx : ds.blocks_flat), st) != cudaSuccess)
     return LR_ERR_CUDA;

@@ -116,6 +116,7 @@ __global__ __launch_bounds__(kOvfThreads) void k_overflow(Ws ws) {
     const long long pidx = pid - V.pix_base;
     const int px = (int)(pidx % V.width), py = (int)(pidx / V.width);
     const int bin_g = V.bin_base + (py >> kBinLog2) * V.nbx + (px >> kBinLog2);
+    const int hb = ((py & (kBin - 1)) / kHbH) * (kBin / kHbW) + (px & (kBin - 1)) / kHbW;
     const uint32_t off = ws.bin_off[bin_g];
     const int n = (int)(ws.bin_off[bin_g + 1] - off);
 
@@ -138,7 +139,8 @@ __global__ __launch_bounds__(kOvfThreads) void k_overflow(Ws ws) {
         uint32_t rec = 0;
         if (i < n) {
           rec = ~(uint32_t)ws.refs[off + i];
-          if (rec < (uint64_t)ws.total_quads) {
+          // the reference's half-block bit first (coalesced), the quad's box only then
+          if (((ws.ref_hb[off + i] >> hb) & 1u) && rec < (uint64_t)ws.total_quads) {
             const uint2 r = ws.rec_rect[rec];
             hit = (int)(r.x & 0xffff) <= px && (int)(r.x >> 16) >= px && (int)(r.y & 0xffff) <= py &&
                   (int)(r.y >> 16) >= py;

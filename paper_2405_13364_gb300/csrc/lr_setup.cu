@@ -99,6 +99,7 @@ __global__ __launch_bounds__(256) void k_setup(Ws ws) {
       if (why != kVisible && (worst == kVisible || why < worst)) worst = why;
     }
     uint32_t info = 0;
+    float rep = 0.f;
     uint2 rect = make_uint2(kRectInvisible, kRectInvisible);
     if (worst == kVisible) {
       const long long a0 = area2(X[0], Y[0], X[1], Y[1], X[2], Y[2]);
@@ -122,6 +123,8 @@ __global__ __launch_bounds__(256) void k_setup(Ws ws) {
           const int bw = (px1 >> kBinLog2) - (px0 >> kBinLog2) + 1;
           const int bh = (py1 >> kBinLog2) - (py0 >> kBinLog2) + 1;
           if (bw > kSmallBins || bh > kSmallBins) info |= kInfoLarge;
+          if (q[0] == q[1] && q[0] == q[2] && q[0] == q[3]) info |= kInfoFlatDepth;
+          rep = rep_depth_of(X, Y, q, info, px0, px1, py0, py1);
         }
       }
     }
@@ -135,6 +138,7 @@ __global__ __launch_bounds__(256) void k_setup(Ws ws) {
     ws.rec_q[g] = make_float4(q[0], q[1], q[2], q[3]);
     ws.rec_rect[g] = rect;
     ws.rec_info[g] = info | (worst << 8);
+    ws.rec_rep[g] = rep;
     if (bad) set_error(ws.ctrl, LR_ERR_INVALID_ARG);
   }
   // per-warp statistics: one atomic per reason present in the warp
