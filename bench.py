@@ -35,6 +35,17 @@ WORKLOAD = "layers-1080p: 1920x1080, 32 wavy layers x 256x128 = 1,048,576 indexe
 # multiplies + 2 adds = 8, sorter = K compare/selects, blend = 8 fp32 ops
 OPS_PER_FRAG_BASE = 25
 SM_COUNT = 152
+# kernels launched per frame: k_write_views, k_init, k_setup, k_bin_count, k_bin_scan,
+# k_bin_scatter, k_bin_sort, k_bin_sort_big, k_raster, k_overflow
+LAUNCHES_PER_FRAME = 10
+# DRAM bytes (read + write) per k_raster launch from ncu captures (profiles/), keyed by
+# (workload, K, carried colours), with the hash of the rasteriser sources they were taken
+# on: the figure is reported only while the kernel is unchanged.
+RASTER_TRAFFIC = {
+    ("layers", 1, False): (97_134_848, "0ff37abe839e698e"),      # profiles/k_raster_layers1080p.md
+    ("particles", 1, False): (586_412_032, "0ff37abe839e698e"),  # profiles/k_raster_particles1080p.md
+}
+RASTER_SOURCES = ("lr_raster.cuh", "lr_common.cuh")
 LANES_PER_SM_CLK = 128
 
 
@@ -75,38 +86,66 @@ def _measured_peaks():
         return None
 
 
+def raster_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2405_13364_gb300", "csrc")
+    for f in RASTER_SOURCES:
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def raster_traffic(workload: str, k: int, carry: bool):
+    t = RASTER_TRAFFIC.get((workload, k, carry))
+    if t is None or t[1] != raster_source_hash():
+        return None
+    return t[0]
+
+
 class ClockSampler:
-    """Samples nvidia-smi clocks / throttle reasons in the background during timing."""
+    """Samples SM clocks and throttle reasons during timing with one `nvidia-smi -lms`
+    process (started before the timed region, stopped after it)."""
 
-    def __init__(self, index: int):
-        self.index = index
-        self.samples = []
-        self._stop = threading.Event()
-        self._t = None
-
-    def _run(self):
-        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
              "clocks_event_reasons.sw_power_cap")
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                      "--format=csv,noheader,nounits"], capture_output=True,
-                                     text=True, timeout=5).stdout.strip()
-                if out:
-                    self.samples.append([x.strip() for x in out.split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+
+    def __init__(self, index: int, period_ms: int = 50):
+        self.index = index
+        self.period_ms = period_ms
+        self.samples = []
+        self._proc = None
+        self._t = None
+
+    def _read(self):
+        for line in self._proc.stdout:
+            f = [x.strip() for x in line.strip().split(",")]
+            if len(f) >= 7:
+                self.samples.append(f)
 
     def __enter__(self):
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+        try:
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            time.sleep(0.15)            # the first sample lands before the timed work starts
+        except Exception:
+            self._proc = None
         return self
 
     def __exit__(self, *a):
-        self._stop.set()
-        self._t.join(timeout=10)
+        if self._proc is not None:
+            time.sleep(0.06)            # one more sample at the end of the timed region
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
+            self._t.join(timeout=5)
 
     def summary(self):
         if not self.samples:
@@ -118,7 +157,7 @@ class ClockSampler:
                           if len(s) > 3 + i and s[3 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.samples)}
+                "samples": len(self.samples), "period_ms": self.period_ms}
 
 
 def serving_benchmark(P, torch, num_requests=256, rate_hz=200.0, seed=0):
@@ -410,7 +449,7 @@ def run_gpu(args):
         "overflow_pixels": st0["overflow_pixels"],
         "roofline": {"bound": "alu", "kernel": "k_raster", "achieved": round(achieved, 4),
                      "peak": round(peak, 3), "unit": "Tlane-op/s", "frac": round(achieved / peak, 4),
-                     "traffic": None,
+                     "traffic": raster_traffic(args.workload, args.k, carry),
                      "ops_per_fragment": OPS_PER_FRAG_BASE + args.k,
                      "peak_basis": f"{SM_COUNT} SMs x 128 lanes x {sm_max:.0f} MHz (max SM clock)"},
         "setup_hbm": None,
@@ -418,7 +457,7 @@ def run_gpu(args):
         "e2e": {"value": round(e2e_value, 3), "unit": "Gfrag/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4)},
         "served_stream": serving,
-        "gpu_launches": 9 * args.steps,
+        "gpu_launches": LAUNCHES_PER_FRAME * args.steps,
         "clocks": clocks,
     }
     if peaks:
@@ -462,7 +501,7 @@ def run_profile(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--k", type=int, default=0, help="sorter capacity K; 0 = autotuned")
