@@ -119,15 +119,18 @@ static long long default_refs(const Layout& L, int ref_factor) {
   return std::min((long long)ref_factor * L.total_quads + 64LL * L.total_bins + 1024, kMaxRefs);
 }
 
-// per reference: the sort key, its merge buffer slot and its half-block mask
+// per reference: the sort key, its merge buffer slot and its word of the half-block
+// bitmap (plus up to 32 padding words per bin)
 static size_t bytes_for_refs(const Layout& L, long long refs) {
-  return L.refs + align256(sizeof(unsigned long long) * (size_t)refs) * 2 + align256(sizeof(uint32_t) * (size_t)refs);
+  return L.refs + align256(sizeof(unsigned long long) * (size_t)refs) * 2 +
+         align256(sizeof(uint32_t) * ((size_t)refs + 32 * (size_t)L.total_bins));
 }
 
 // capacity from the bytes available, placing refs_tmp and ref_hb after refs
 static void set_capacity(Layout& L, size_t ws_bytes) {
   long long cap = 0;
-  if (ws_bytes > L.refs) cap = (long long)((ws_bytes - L.refs) / (2 * sizeof(unsigned long long) + sizeof(uint32_t)));
+  const size_t fixed = L.refs + 32 * sizeof(uint32_t) * (size_t)L.total_bins + 1024;
+  if (ws_bytes > fixed) cap = (long long)((ws_bytes - fixed) / (2 * sizeof(unsigned long long) + sizeof(uint32_t)));
   cap = std::min(cap, kMaxRefs);
   cap &= ~63LL;
   while (cap > 0 && bytes_for_refs(L, cap) > ws_bytes) cap -= 64;

@@ -281,17 +281,23 @@ __device__ void cta_merge(const unsigned long long* a, int na, const unsigned lo
   }
 }
 
-// For every sorted reference of a bin, the 32-bit mask of the bin's 8x4 half-blocks
-// (bit hy * 4 + hx) that the quad's pixel AABB overlaps; the rasteriser's per-half-block
-// filter then tests one bit instead of gathering the quad's rectangle.
-__device__ void write_hb_masks(const Ws& ws, const unsigned long long* r, uint32_t* hb, int n, int bin) {
+// The bin's transposed half-block bitmap (hb_row): for each sorted reference, the 32-bit
+// mask of the bin's 8x4 half-blocks (bit hy * 4 + hx) that the quad's pixel AABB overlaps,
+// computed one warp per 32 references and transposed across the warp, so that row h, word
+// w holds the bits of references 32 w .. 32 w + 31 for half-block h. The rasteriser then
+// reads a half-block's candidates with one coalesced load per 1024 references.
+__device__ void write_hb_bitmap(const Ws& ws, const unsigned long long* r, int n, int bin) {
   const int v = view_of_bin(ws.views, ws.n_views, bin);
   const ViewDev& V = ws.views[v];
   const int b = bin - V.bin_base;
   const int x0 = (b % V.nbx) << kBinLog2, y0 = (b / V.nbx) << kBinLog2;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const uint32_t rec = ~(uint32_t)r[i];
+  const int nw = (n + 31) >> 5;
+  const int lane = threadIdx.x & 31;
+  uint32_t* bm = ws.ref_hb + (r - ws.refs) + 32 * (size_t)bin;
+  for (int w = threadIdx.x >> 5; w < nw; w += blockDim.x >> 5) {
+    const int i = 32 * w + lane;
     uint32_t mask = 0;
+    const uint32_t rec = i < n ? ~(uint32_t)r[i] : 0xFFFFFFFFu;
     if (rec < (uint64_t)ws.total_quads) {
       const uint2 rc = ws.rec_rect[rec];
       const int px0 = max((int)(rc.x & 0xffff), x0) - x0, px1 = min((int)(rc.x >> 16), x0 + kBin - 1) - x0;
@@ -302,7 +308,7 @@ __device__ void write_hb_masks(const Ws& ws, const unsigned long long* r, uint32
         for (int hy = hy0; hy <= hy1; ++hy) mask |= row << (hy * (kBin / kHbW));
       }
     }
-    hb[i] = mask;
+    bm[(size_t)lane * nw + w] = warp_transpose32(mask, lane);
   }
 }
 
@@ -396,7 +402,7 @@ __global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {
     cta_sort(r, n, sbuf);
     __syncthreads();
   }
-  write_hb_masks(ws, r, ws.ref_hb + off, n, bin);
+  write_hb_bitmap(ws, r, n, bin);
 }
 
 // Ascending merge sort of g[0, n) (n <= kSortBigCap) in shared memory by the whole CTA:
@@ -487,7 +493,7 @@ __global__ __launch_bounds__(kSortBigThreads) void k_bin_sort_big(Ws ws) {
       for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = src[i];
     }
     __syncthreads();
-    write_hb_masks(ws, r, ws.ref_hb + off, n, bin);
+    write_hb_bitmap(ws, r, n, bin);
     __syncthreads();
   }
 }

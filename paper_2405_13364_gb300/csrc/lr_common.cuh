@@ -101,12 +101,82 @@ struct Ws {
   uint32_t* bin_order;       // [total_bins]: bins by decreasing reference count
   unsigned long long* refs;      // [refs_cap] sorted per bin: (~rep_bits << 32) | ~record
   unsigned long long* refs_tmp;  // [refs_cap] merge buffer of the high-density sort
-  uint32_t* ref_hb;          // [refs_cap] half-blocks of its bin that reference i's AABB overlaps
+  uint32_t* ref_hb;          // [refs_cap + 32 * total_bins] per bin, the transposed half-block
+                             // bitmap of its sorted references (hb_row)
   uint32_t* ovf_list;        // [total_pix] flattened pixel ids registered for the exact path
   // backward
   const float* grad_out;     // f32[H][W][4] of view 0
   const float* fwd;          // f32[H][W][4] of view 0
   float* grad_col;           // f32[Q][4] of view 0
+};
+
+// 32x32 bit-matrix transpose across a warp: lane r holds row r on entry (bit c = element
+// (r, c)) and column r on exit (bit c = element (c, r)); five butterfly exchanges.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+  const uint32_t m[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int j = 16 >> i;
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? ((x & ~m[i]) | ((y >> j) & m[i])) : ((x & m[i]) | ((y & m[i]) << j));
+  }
+  return x;
+}
+
+// The half-block bitmap of a bin with n sorted references starting at off: row h (one per
+// 8x4 half-block) holds nw = ceil(n / 32) words, bit j of word w set iff reference 32 w + j
+// overlaps half-block h. Rows of bin b start at off + 32 b, so the bitmaps of all bins fit
+// in refs + 32 * bins words.
+__device__ __forceinline__ const uint32_t* hb_row(const Ws& ws, uint32_t off, int bin, int n, int hb) {
+  return ws.ref_hb + (size_t)off + 32 * (size_t)bin + (size_t)hb * (size_t)((n + 31) >> 5);
+}
+
+// Position of the k-th (0-based) set bit of m; k < popc(m).
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int k) {
+  int pos = 0;
+#pragma unroll
+  for (int w = 16; w > 0; w >>= 1) {
+    const int lc = __popc(m & ((1u << w) - 1u));
+    if (k >= lc) {
+      k -= lc;
+      m >>= w;
+      pos += w;
+    }
+  }
+  return pos;
+}
+
+// Hands out the set bits of up to 32 bitmap words (one per lane, `word`) in order, 32 at a
+// time: after prepare(), round r gives lane L the (32 r + L)-th set bit overall as a bit
+// index 32 * (word's lane) + position, or -1 past the end.
+struct BitRounds {
+  uint32_t word;
+  int incl;     // inclusive prefix of the set-bit counts over lanes
+  int total;
+  __device__ __forceinline__ void prepare(uint32_t w, int lane) {
+    word = w;
+    incl = __popc(w);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    total = __shfl_sync(0xffffffffu, incl, 31);
+  }
+  __device__ __forceinline__ int get(int r0, int lane) const {
+    const int p = r0 + lane;
+    int s = 0;   // number of lanes whose inclusive count is <= p = the lane holding bit p
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int v = __shfl_sync(0xffffffffu, incl, s + step - 1);
+      if (v <= p) s += step;
+    }
+    s = min(s, 31);
+    const uint32_t ws = __shfl_sync(0xffffffffu, word, s);
+    const int before = __shfl_sync(0xffffffffu, incl, s) - __popc(ws);
+    if (p >= total) return -1;
+    return 32 * s + nth_set_bit(ws, p - before);
+  }
 };
 
 __device__ __forceinline__ void set_error(Ctrl* c, int code) { atomicCAS(&c->error, 0, code); }

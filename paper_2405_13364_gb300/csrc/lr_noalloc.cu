@@ -104,7 +104,10 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
   const size_t o_ord = o; o = up256(o + 4 * (size_t)nbins);
   const size_t o_ovf = o; o = up256(o + 4 * (size_t)npix);
   if (o >= (size_t)LR_NOALLOC_SCRATCH_BYTES) return LR_ERR_TOO_LARGE;
-  long long cap = (long long)(((size_t)LR_NOALLOC_SCRATCH_BYTES - o - 1024) / 20) & ~63LL;
+  // per reference 8 B key + 8 B merge slot + 4 B bitmap word, plus 32 bitmap words per bin
+  const size_t fixed_hb = 128 * (size_t)nbins + 2048;
+  if (o + fixed_hb >= (size_t)LR_NOALLOC_SCRATCH_BYTES) return LR_ERR_TOO_LARGE;
+  long long cap = (long long)(((size_t)LR_NOALLOC_SCRATCH_BYTES - o - fixed_hb) / 20) & ~63LL;
   if (cap > 0xFFFFFF00LL) cap = 0xFFFFFF00LL;
   // require room for at least two references per quad and one per bin
   if (cap < 2 * Q + nbins + 1024) return LR_ERR_TOO_LARGE;

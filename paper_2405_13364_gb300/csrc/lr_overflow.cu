@@ -3,13 +3,17 @@
 // by one and notes they "could be registered and afterwards processed by a slower,
 // conservative algorithm" (Sec. 2, "Sample blending"; Sec. 3, "Fragment sorting errors").
 //
-// One warp per registered pixel. The warp re-gathers every fragment covering the pixel
-// from its bin's reference list (exact 64-bit edge tests, the same depth key as the
-// rasteriser), sorts them fully and composites front to back. Memory is bounded: a pass
-// keeps the kOvfKeep nearest fragments below a threshold in a shared-memory buffer (when
-// the buffer fills, it is sorted and cut back to kOvfKeep), composites them, lowers the
-// threshold to the last composited key and repeats until no fragment is left. Any depth
-// complexity is handled, at one re-scan of the bin per kOvfKeep fragments.
+// One warp per registered pixel. The warp takes the candidates of the pixel's half-block
+// from the bin's transposed bitmap (one coalesced load per 1024 references), keeps those
+// whose box holds the pixel, re-evaluates their fragments exactly (64-bit edge tests, the
+// same depth key as the rasteriser), sorts them fully and composites front to back. The
+// overflow pixels of a frame are few and all run in one wave, so the kernel's time is one
+// warp's chain of dependent loads: the bitmap keeps that chain to a few loads per 32
+// candidates. Memory is bounded: a pass keeps the kOvfKeep nearest fragments below a
+// threshold in a shared-memory buffer (when the buffer fills, it is sorted and cut back to
+// kOvfKeep), composites them, lowers the threshold to the last composited key and repeats
+// until no fragment is left. Any depth complexity is handled, at one re-scan of the
+// candidates per kOvfKeep fragments.
 #include "lr_raster.cuh"
 
 namespace lr {
@@ -95,56 +99,107 @@ __device__ __forceinline__ int pow2_at_least(int n) {
   return p;
 }
 
-// BWD: instead of writing the pixel, accumulate the gradient of the flat per-quad RGBA
-// (same formulas as the rasteriser's backward), with each lane walking its segment of the
-// sorted fragments from the exact prefix (colour, transmittance) of the lanes before it.
-template <bool BWD>
-__global__ __launch_bounds__(kOvfThreads) void k_overflow(Ws ws) {
-  __shared__ unsigned long long sbuf[kOvfThreads / 32][kOvfBuf];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long* buf = sbuf[warp];
-  if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
-  const unsigned long long total = ws.ctrl->ovf_count;
-  for (;;) {
-    unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(&ws.ctrl->ovf_head, 1ull);
-    item = __shfl_sync(0xffffffffu, item, 0);
-    if (item >= total) break;
-    const long long pid = ws.ovf_list[item];
-    const int v = view_of_pixel(ws.views, ws.n_views, pid);
-    const ViewDev& V = ws.views[v];
-    const long long pidx = pid - V.pix_base;
-    const int px = (int)(pidx % V.width), py = (int)(pidx / V.width);
-    const int bin_g = V.bin_base + (py >> kBinLog2) * V.nbx + (px >> kBinLog2);
-    const int hb = ((py & (kBin - 1)) / kHbH) * (kBin / kHbW) + (px & (kBin - 1)) / kHbW;
-    const uint32_t off = ws.bin_off[bin_g];
-    const int n = (int)(ws.bin_off[bin_g + 1] - off);
-
-    float cr = 0.f, cg = 0.f, cb = 0.f, T = 1.f;
-    unsigned long long tau = kSent;   // exclusive upper bound of the fragments still to do
-    GradPixel gp;
-    if (BWD) {
-      const float4 gq = reinterpret_cast<const float4*>(ws.grad_out)[pidx];
-      const float4 fq = reinterpret_cast<const float4*>(ws.fwd)[pidx];
-      gp.gr = gq.x; gp.gg = gq.y; gp.gb = gq.z; gp.ga = gq.w;
-      gp.fr = fq.x; gp.fg = fq.y; gp.fb = fq.z; gp.fT = 1.0f - fq.w;
-      gp.grad = ws.grad_col;
+// Front-to-back composite of the sorted fragments buf[0, m) of pixel (px, py) onto the
+// running (cr, cg, cb, T): each lane composites a contiguous segment, then an inclusive
+// scan of (C, T) pairs with (C1, T1) o (C2, T2) = (C1 + T1 C2, T1 T2) combines them in
+// order. With grad, also accumulates the per-quad RGBA gradient (flat colours): each lane
+// walks its segment again from the exact prefix of the lanes before it.
+__device__ void composite_sorted(const Ws& ws, const ViewDev& V, const unsigned long long* buf, int m, int px,
+                                 int py, float& cr, float& cg, float& cb, float& T, const GradPixel* gp) {
+  const int lane = threadIdx.x & 31;
+  const int seg = (m + 31) / 32;
+  float sr = 0.f, sg = 0.f, sb = 0.f, sT = 1.f;
+  for (int k = lane * seg; k < min(m, (lane + 1) * seg); ++k) {
+    const unsigned long long sk = buf[k];
+    const uint32_t id = (uint32_t)sk;
+    float4 col;
+    unsigned long long dummy;
+    frag_eval(ws, V, (uint32_t)(V.quad_base + (id >> 1)), (int)(id & 1u), px, py, &dummy, &col);
+    const float w = sT * col.w;
+    sr += w * col.x; sg += w * col.y; sb += w * col.z;
+    sT *= 1.0f - col.w;
+  }
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float pr = __shfl_up_sync(0xffffffffu, sr, o), pg = __shfl_up_sync(0xffffffffu, sg, o);
+    const float pb = __shfl_up_sync(0xffffffffu, sb, o), pT = __shfl_up_sync(0xffffffffu, sT, o);
+    if (lane >= o) {
+      sr = pr + pT * sr; sg = pg + pT * sg; sb = pb + pT * sb; sT = pT * sT;
     }
-    for (;;) {
-      int nbuf = 0, below = 0;
-      unsigned long long lb = 0;     // exclusive lower bound once the buffer was cut back
-      for (int base = 0; base < n; base += 32) {
-        const int i = base + lane;
+  }
+  if (gp) {
+    float er = __shfl_up_sync(0xffffffffu, sr, 1), eg = __shfl_up_sync(0xffffffffu, sg, 1);
+    float eb = __shfl_up_sync(0xffffffffu, sb, 1), eT = __shfl_up_sync(0xffffffffu, sT, 1);
+    if (lane == 0) { er = eg = eb = 0.f; eT = 1.f; }
+    float wr = cr + T * er, wg = cg + T * eg, wb = cb + T * eb, wT = T * eT;
+    for (int k = lane * seg; k < min(m, (lane + 1) * seg); ++k) {
+      const uint32_t id = (uint32_t)buf[k];
+      const uint32_t j = id >> 1;
+      const float4 col = __ldg(reinterpret_cast<const float4*>(V.col) + j);
+      const float w = wT * col.w;
+      wr += w * col.x; wg += w * col.y; wb += w * col.z;
+      const float om = 1.0f - col.w;
+      float da = gp->gr * wT * col.x + gp->gg * wT * col.y + gp->gb * wT * col.z;
+      if (om > 1e-6f) {
+        const float inv = 1.0f / om;
+        da -= (gp->gr * (gp->fr - wr) + gp->gg * (gp->fg - wg) + gp->gb * (gp->fb - wb)) * inv;
+        da += gp->ga * gp->fT * inv;
+      }
+      float* gq = gp->grad + 4ull * j;
+      atomicAdd(gq + 0, gp->gr * w);
+      atomicAdd(gq + 1, gp->gg * w);
+      atomicAdd(gq + 2, gp->gb * w);
+      atomicAdd(gq + 3, da);
+      wT *= om;
+    }
+  }
+  sr = __shfl_sync(0xffffffffu, sr, 31); sg = __shfl_sync(0xffffffffu, sg, 31);
+  sb = __shfl_sync(0xffffffffu, sb, 31); sT = __shfl_sync(0xffffffffu, sT, 31);
+  cr += T * sr; cg += T * sg; cb += T * sb; T *= sT;
+}
+
+// The exact path for one pixel (flattened id pid) by one warp, with buf a kOvfBuf-entry
+// shared-memory buffer. BWD: instead of writing the pixel, accumulate the gradient of the
+// flat per-quad RGBA (same formulas as the rasteriser's backward).
+template <bool BWD>
+__device__ void overflow_pixel(const Ws& ws, long long pid, unsigned long long* buf) {
+  const int lane = threadIdx.x & 31;
+  const int v = view_of_pixel(ws.views, ws.n_views, pid);
+  const ViewDev& V = ws.views[v];
+  const long long pidx = pid - V.pix_base;
+  const int px = (int)(pidx % V.width), py = (int)(pidx / V.width);
+  const int bin_g = V.bin_base + (py >> kBinLog2) * V.nbx + (px >> kBinLog2);
+  const int hb = ((py & (kBin - 1)) / kHbH) * (kBin / kHbW) + (px & (kBin - 1)) / kHbW;
+  const uint32_t off = ws.bin_off[bin_g];
+  const int n = (int)(ws.bin_off[bin_g + 1] - off);
+
+  float cr = 0.f, cg = 0.f, cb = 0.f, T = 1.f;
+  unsigned long long tau = kSent;   // exclusive upper bound of the fragments still to do
+  GradPixel gp;
+  if (BWD) {
+    const float4 gq = reinterpret_cast<const float4*>(ws.grad_out)[pidx];
+    const float4 fq = reinterpret_cast<const float4*>(ws.fwd)[pidx];
+    gp.gr = gq.x; gp.gg = gq.y; gp.gb = gq.z; gp.ga = gq.w;
+    gp.fr = fq.x; gp.fg = fq.y; gp.fb = fq.z; gp.fT = 1.0f - fq.w;
+    gp.grad = ws.grad_col;
+  }
+  for (;;) {
+    int nbuf = 0, below = 0;
+    unsigned long long lb = 0;     // exclusive lower bound once the buffer was cut back
+    const uint32_t* row = hb_row(ws, off, bin_g, n, hb);
+    const int nw = (n + 31) >> 5;
+    for (int g = 0; g < nw; g += 32) {
+      BitRounds br;
+      br.prepare(g + lane < nw ? __ldg(row + g + lane) : 0u, lane);
+      for (int r0 = 0; r0 < br.total; r0 += 32) {
+        const int j = br.get(r0, lane);
         bool hit = false;
         uint32_t rec = 0;
-        if (i < n) {
-          rec = ~(uint32_t)ws.refs[off + i];
-          // the reference's half-block bit first (coalesced), the quad's box only then
-          if (((ws.ref_hb[off + i] >> hb) & 1u) && rec < (uint64_t)ws.total_quads) {
-            const uint2 r = ws.rec_rect[rec];
-            hit = (int)(r.x & 0xffff) <= px && (int)(r.x >> 16) >= px && (int)(r.y & 0xffff) <= py &&
-                  (int)(r.y >> 16) >= py;
-          }
+        if (j >= 0) {
+          rec = ~(uint32_t)ws.refs[off + 32 * g + j];
+          const uint2 r = ws.rec_rect[rec];
+          hit = (int)(r.x & 0xffff) <= px && (int)(r.x >> 16) >= px && (int)(r.y & 0xffff) <= py &&
+                (int)(r.y >> 16) >= py;
         }
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
@@ -166,69 +221,34 @@ __global__ __launch_bounds__(kOvfThreads) void k_overflow(Ws ws) {
           }
         }
       }
-      const int n2 = pow2_at_least(nbuf);
-      for (int k = nbuf + lane; k < n2; k += 32) buf[k] = 0ull;
-      __syncwarp();
-      warp_sort_desc(buf, n2);
-      const int m = min(nbuf, kOvfKeep);
-      // composite buf[0, m) front to back: per-lane segments, then an ordered combine
-      const int seg = (m + 31) / 32;
-      float sr = 0.f, sg = 0.f, sb = 0.f, sT = 1.f;
-      for (int k = lane * seg; k < min(m, (lane + 1) * seg); ++k) {
-        const unsigned long long sk = buf[k];
-        const uint32_t id = (uint32_t)sk;
-        float4 col;
-        unsigned long long dummy;
-        frag_eval(ws, V, (uint32_t)(V.quad_base + (id >> 1)), (int)(id & 1u), px, py, &dummy, &col);
-        const float w = sT * col.w;
-        sr += w * col.x; sg += w * col.y; sb += w * col.z;
-        sT *= 1.0f - col.w;
-      }
-      // inclusive scan of (C, T) pairs with (C1, T1) o (C2, T2) = (C1 + T1 C2, T1 T2)
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const float pr = __shfl_up_sync(0xffffffffu, sr, o), pg = __shfl_up_sync(0xffffffffu, sg, o);
-        const float pb = __shfl_up_sync(0xffffffffu, sb, o), pT = __shfl_up_sync(0xffffffffu, sT, o);
-        if (lane >= o) {
-          sr = pr + pT * sr; sg = pg + pT * sg; sb = pb + pT * sb; sT = pT * sT;
-        }
-      }
-      if (BWD) {
-        // exclusive prefix of this lane's segment, then walk it again with exact state
-        float er = __shfl_up_sync(0xffffffffu, sr, 1), eg = __shfl_up_sync(0xffffffffu, sg, 1);
-        float eb = __shfl_up_sync(0xffffffffu, sb, 1), eT = __shfl_up_sync(0xffffffffu, sT, 1);
-        if (lane == 0) { er = eg = eb = 0.f; eT = 1.f; }
-        float wr = cr + T * er, wg = cg + T * eg, wb = cb + T * eb, wT = T * eT;
-        for (int k = lane * seg; k < min(m, (lane + 1) * seg); ++k) {
-          const uint32_t id = (uint32_t)buf[k];
-          const uint32_t j = id >> 1;
-          const float4 col = __ldg(reinterpret_cast<const float4*>(V.col) + j);
-          const float w = wT * col.w;
-          wr += w * col.x; wg += w * col.y; wb += w * col.z;
-          const float om = 1.0f - col.w;
-          float da = gp.gr * wT * col.x + gp.gg * wT * col.y + gp.gb * wT * col.z;
-          if (om > 1e-6f) {
-            const float inv = 1.0f / om;
-            da -= (gp.gr * (gp.fr - wr) + gp.gg * (gp.fg - wg) + gp.gb * (gp.fb - wb)) * inv;
-            da += gp.ga * gp.fT * inv;
-          }
-          float* gq = gp.grad + 4ull * j;
-          atomicAdd(gq + 0, gp.gr * w);
-          atomicAdd(gq + 1, gp.gg * w);
-          atomicAdd(gq + 2, gp.gb * w);
-          atomicAdd(gq + 3, da);
-          wT *= om;
-        }
-      }
-      sr = __shfl_sync(0xffffffffu, sr, 31); sg = __shfl_sync(0xffffffffu, sg, 31);
-      sb = __shfl_sync(0xffffffffu, sb, 31); sT = __shfl_sync(0xffffffffu, sT, 31);
-      cr += T * sr; cg += T * sg; cb += T * sb; T *= sT;
-      if (below <= kOvfKeep || m == 0) break;
-      tau = buf[m - 1];
-      __syncwarp();
     }
-    if (!BWD && lane == 0) write_pixel(V, pidx, cr, cg, cb, T);
+    const int n2 = pow2_at_least(nbuf);
+    for (int k = nbuf + lane; k < n2; k += 32) buf[k] = 0ull;
     __syncwarp();
+    warp_sort_desc(buf, n2);
+    const int m = min(nbuf, kOvfKeep);
+    composite_sorted(ws, V, buf, m, px, py, cr, cg, cb, T, BWD ? &gp : nullptr);
+    if (below <= kOvfKeep || m == 0) break;
+    tau = buf[m - 1];
+    __syncwarp();
+  }
+  if (!BWD && lane == 0) write_pixel(V, pidx, cr, cg, cb, T);
+  __syncwarp();
+}
+
+// the exact path over the registered pixel list
+template <bool BWD>
+__global__ __launch_bounds__(kOvfThreads) void k_overflow(Ws ws) {
+  __shared__ unsigned long long sbuf[kOvfThreads / 32][kOvfBuf];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
+  const unsigned long long total = ws.ctrl->ovf_count;
+  for (;;) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(&ws.ctrl->ovf_head, 1ull);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= total) break;
+    overflow_pixel<BWD>(ws, (long long)ws.ovf_list[item], sbuf[warp]);
   }
 }
 

@@ -8,16 +8,18 @@
 //
 // Per half-block (all from the bin's reference list, already sorted front to back by
 // k_bin_sort -- stage 1 of the two-stage sort):
-//   1. filter: 32 references at a time, test the reference's half-block bit (precomputed
-//      per reference by k_bin_sort), and queue the hits in shared memory, order preserved;
-//   2. triangle setup, lane-parallel: for 32 queued quads, both triangles' integer edge
+//   1. candidates: the half-block's row of the bin's transposed bitmap (written by
+//      k_bin_sort: bit j set iff sorted reference j overlaps the half-block) is read with
+//      one coalesced load per 1024 references, and its set bits are handed out 32 at a
+//      time in sorted order, one candidate quad per lane;
+//   2. triangle setup, lane-parallel: for 32 candidate quads, both triangles' integer edge
 //      functions at the half-block origin, per-pixel steps, 1/area, depth-plane deltas;
 //      a triangle whose edge values stay below 2^30 on the half-block is marked "fast"
 //      and evaluated with 32-bit integers, others with exact 64-bit integers; the same
 //      lane computes each triangle's 32-pixel coverage mask (top-left rule) row by row;
 //   3. coverage, transposed: a 32x32 bit transpose across the warp turns "triangle ->
 //      pixels" into "pixel -> triangles", one bit per covering triangle in each lane;
-//   4. fragments, per lane in queue order: the exact depth key of the fragment
+//   4. fragments, per lane in candidate order: the exact depth key of the fragment
 //      (interpolated 1/w, identical bit for bit to the oracle's formula) is pushed into a
 //      K-slot register sorter (stage 2, the paper's "depth filter"). When full,
 //      the nearest element is evicted and blended front to back. If a fragment arrives
@@ -57,11 +59,10 @@ struct __align__(16) TriSm {
   int pad[2];
 };
 
-// dynamic shared memory of k_raster: per warp 64 triangle records, a 64-entry candidate
-// queue and, when fragments carry colours, 3 premultiplied vertex colours per triangle
+// dynamic shared memory of k_raster: per warp 64 triangle records and, when fragments
+// carry colours, 3 premultiplied vertex colours per triangle
 __host__ __device__ constexpr size_t raster_smem_bytes(bool vtx) {
-  return (size_t)kRasterWarps * 64 * (sizeof(TriSm) + sizeof(uint32_t)) +
-         (vtx ? (size_t)kRasterWarps * 64 * 3 * sizeof(float4) : 0);
+  return (size_t)kRasterWarps * 64 * sizeof(TriSm) + (vtx ? (size_t)kRasterWarps * 64 * 3 * sizeof(float4) : 0);
 }
 
 // exact 64-bit edge values (unbiased) of a triangle at pixel (px, py)
@@ -197,17 +198,29 @@ static __device__ __noinline__ uint32_t tri_mask_slow(const TriSm& T, int ox, in
   return mask;
 }
 
-// 32x32 bit-matrix transpose across a warp: lane r holds row r on entry (bit c = element
-// (r, c)) and column r on exit (bit c = element (c, r)); five butterfly exchanges.
-__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
-  const uint32_t m[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const int j = 16 >> i;
-    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
-    x = (lane & j) ? ((x & ~m[i]) | ((y >> j) & m[i])) : ((x & m[i]) | ((y & m[i]) << j));
+// Exact depth key (interpolated 1/w, Sec. 2 "Stage 3", the reading O.8 of the depth
+// formula) of a triangle record at pixel (px, py) = (ox + lx, oy + ly) of its half-block;
+// also returns the barycentric weights l1, l2 it used.
+__device__ __forceinline__ float tri_key(const TriSm& T, int4 ea, int4 eb, float4 kq, int lx, int ly, int px,
+                                         int py, float& l1, float& l2) {
+  const uint32_t fl = (uint32_t)eb.z;
+  float f1, f2;
+  if (fl & kTriFast) {
+    const int e1 = (int)((uint32_t)ea.x + (uint32_t)lx * (uint32_t)ea.z + (uint32_t)ly * (uint32_t)eb.x +
+                         ((fl >> 4) & 1u));
+    const int e2 = (int)((uint32_t)ea.y + (uint32_t)lx * (uint32_t)ea.w + (uint32_t)ly * (uint32_t)eb.y +
+                         ((fl >> 5) & 1u));
+    f1 = __int2float_rn(e1);
+    f2 = __int2float_rn(e2);
+  } else {
+    long long e[3];
+    edges64(T, px, py, e);
+    f1 = __ll2float_rn(e[1]);
+    f2 = __ll2float_rn(e[2]);
   }
-  return x;
+  l1 = __fmul_rn(f1, kq.w);
+  l2 = __fmul_rn(f2, kq.w);
+  return __fadd_rn(kq.x, __fadd_rn(__fmul_rn(l1, kq.y), __fmul_rn(l2, kq.z)));
 }
 
 template <int K, bool VTX, bool BWD = false>
@@ -309,9 +322,7 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lx = lane & (kHbW - 1), ly = lane >> 3;
   TriSm* tris = reinterpret_cast<TriSm*>(smem) + warp * 64;
-  uint32_t* cand = reinterpret_cast<uint32_t*>(smem + (size_t)kRasterWarps * 64 * sizeof(TriSm)) + warp * 64;
-  float4* qcs = reinterpret_cast<float4*>(smem + (size_t)kRasterWarps * 64 * (sizeof(TriSm) + 4)) +
-                (size_t)warp * 64 * 3;
+  float4* qcs = reinterpret_cast<float4*>(smem + (size_t)kRasterWarps * 64 * sizeof(TriSm)) + (size_t)warp * 64 * 3;
   if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
   const unsigned long long nitems = ws.ctrl->raster_items;
   unsigned long long frag_total = 0;
@@ -348,11 +359,11 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
     uint32_t cnt = 0;
     unsigned long long hsh = 0;
 
-    auto process = [&](int nc) {
+    auto process = [&](int nc, uint32_t ref) {
       // ---- 2. triangle setup and coverage masks, one quad per lane ---------------------
       uint32_t tm0 = 0, tm1 = 0;
       if (lane < nc) {
-        const uint32_t rec = cand[lane];
+        const uint32_t rec = ~(uint32_t)ws.refs[off + ref];
         const int4 A = ws.rec_xy[2ull * rec], B = ws.rec_xy[2ull * rec + 1];
         const float4 Qv = ws.rec_q[rec];
         const uint32_t info = ws.rec_info[rec];
@@ -392,7 +403,7 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
       // ---- 3. transpose: lane = pixel, bit c = covered by triangle t of quad c -----------
       uint32_t m0 = warp_transpose32(tm0, lane), m1 = warp_transpose32(tm1, lane);
       if (!pix_ok) m0 = m1 = 0;
-      // ---- 4. fragments in queue order through the K-slot sorter ---------------------
+      // ---- 4. fragments in candidate order through the K-slot sorter -----------------
       uint32_t bits = m0 | m1;
       while (bits) {
         const int c = __ffs(bits) - 1;
@@ -405,23 +416,8 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
           const int4 ea = T.ea, eb = T.eb;
           const float4 kq = T.kq;
           const uint32_t fl = (uint32_t)eb.z, id = (uint32_t)eb.w;
-          float f1, f2;
-          if (fl & kTriFast) {
-            const int e1 = (int)((uint32_t)ea.x + (uint32_t)lx * (uint32_t)ea.z + (uint32_t)ly * (uint32_t)eb.x +
-                                 ((fl >> 4) & 1u));
-            const int e2 = (int)((uint32_t)ea.y + (uint32_t)lx * (uint32_t)ea.w + (uint32_t)ly * (uint32_t)eb.y +
-                                 ((fl >> 5) & 1u));
-            f1 = __int2float_rn(e1);
-            f2 = __int2float_rn(e2);
-          } else {
-            long long e[3];
-            edges64(T, px, py, e);
-            f1 = __ll2float_rn(e[1]);
-            f2 = __ll2float_rn(e[2]);
-          }
-          const float l1 = __fmul_rn(f1, kq.w);
-          const float l2 = __fmul_rn(f2, kq.w);
-          const float key = __fadd_rn(kq.x, __fadd_rn(__fmul_rn(l1, kq.y), __fmul_rn(l2, kq.z)));
+          float l1, l2;
+          const float key = tri_key(T, ea, eb, kq, lx, ly, px, py, l1, l2);
           const unsigned long long sk = ((unsigned long long)__float_as_uint(key) << 32) | id;
           ++cnt;
           if (V.hash) hsh += splitmix64(id);
@@ -459,30 +455,17 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
       cnt = 0;
       hsh = 0;
     }
-    // ---- 1. filter the bin's sorted references by the half-block rectangle -----------
-    int qn = 0;
-    for (int base = 0; base < n; base += 32) {
-      const int i = base + lane;
-      bool hit = false;
-      uint32_t rec = 0;
-      if (i < n) {
-        rec = ~(uint32_t)ws.refs[off + i];
-        hit = ((ws.ref_hb[off + i] >> hb) & 1u) && rec < (uint64_t)ws.total_quads;
-      }
-      const unsigned m = __ballot_sync(0xffffffffu, hit);
-      if (hit) cand[qn + __popc(m & ((1u << lane) - 1u))] = rec;
-      qn += __popc(m);
-      __syncwarp();
-      if (qn >= 32) {
-        process(32);
-        const uint32_t keep = lane < qn - 32 ? cand[32 + lane] : 0u;
-        __syncwarp();
-        if (lane < qn - 32) cand[lane] = keep;
-        __syncwarp();
-        qn -= 32;
+    // ---- 1. the half-block's candidates: set bits of its bitmap row, in sorted order ----
+    const uint32_t* row = hb_row(ws, off, bin_g, n, hb);
+    const int nw = (n + 31) >> 5;
+    for (int g = 0; g < nw; g += 32) {
+      BitRounds br;
+      br.prepare(g + lane < nw ? __ldg(row + g + lane) : 0u, lane);
+      for (int r0 = 0; r0 < br.total; r0 += 32) {
+        const int j = br.get(r0, lane);
+        process(min(32, br.total - r0), j < 0 ? 0u : (uint32_t)(32 * g + j));
       }
     }
-    if (qn > 0) process(qn);
     if (pass == 0) pre_flagged = st.flagged;
     }
 
