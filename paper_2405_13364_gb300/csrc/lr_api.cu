@@ -74,7 +74,7 @@ static const RasterVariant kVariants[] = {
 };
 
 struct Layout {
-  size_t ctrl, views, rec_xy, rec_q, rec_rect, rec_info, rec_rep, bin_count, bin_off, bin_cursor, bin_order;
+  size_t ctrl, views, rec_xy, rec_q, rec_rect, rec_info, rec_rep, rec_inv, bin_count, bin_off, bin_cursor, bin_order;
   size_t refs, refs_tmp, ref_hb, ovf_list, total;
   long long total_quads = 0, total_pix = 0, refs_cap = 0;
   int total_bins = 0, total_chunks = 0;
@@ -103,6 +103,7 @@ static Layout make_layout(int n, const long long* Q, const int* W, const int* H)
   L.rec_rect = take(sizeof(uint2) * (size_t)L.total_quads);
   L.rec_info = take(sizeof(uint32_t) * (size_t)L.total_quads);
   L.rec_rep = take(sizeof(float) * (size_t)L.total_quads);
+  L.rec_inv = take(sizeof(float2) * (size_t)L.total_quads);
   L.bin_count = take(sizeof(uint32_t) * (size_t)L.total_bins);
   L.bin_off = take(sizeof(uint32_t) * ((size_t)L.total_bins + 1));
   L.bin_cursor = take(sizeof(uint32_t) * (size_t)L.total_bins);
@@ -156,6 +157,7 @@ static Ws make_ws(const Layout& L, void* base, int n_views) {
   w.rec_rect = reinterpret_cast<uint2*>(b + L.rec_rect);
   w.rec_info = reinterpret_cast<uint32_t*>(b + L.rec_info);
   w.rec_rep = reinterpret_cast<float*>(b + L.rec_rep);
+  w.rec_inv = reinterpret_cast<float2*>(b + L.rec_inv);
   w.bin_count = reinterpret_cast<uint32_t*>(b + L.bin_count);
   w.bin_off = reinterpret_cast<uint32_t*>(b + L.bin_off);
   w.bin_cursor = reinterpret_cast<uint32_t*>(b + L.bin_cursor);

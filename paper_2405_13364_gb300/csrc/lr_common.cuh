@@ -37,6 +37,9 @@ constexpr uint32_t kInfoTri0 = 1u;          // triangle 0 has non-zero area
 constexpr uint32_t kInfoTri1 = 2u;          // triangle 1 has non-zero area
 constexpr uint32_t kInfoLarge = 4u;         // bin rectangle larger than kSmallBins^2 bins
 constexpr uint32_t kInfoFlatDepth = 8u;     // all four vertices have the same 1/w
+constexpr uint32_t kInfoSwap0 = 16u;        // triangle t (bit << t): negative area, v1 <-> v2
+constexpr uint32_t kInfoSmall0 = 64u;       // triangle t (bit << t): 32-bit edge values are
+                                            // exact on every half-block its box touches
 constexpr uint32_t kRectInvisible = 0x0000FFFFu;   // rect.x value of a culled quad
 
 struct ViewDev {
@@ -95,6 +98,7 @@ struct Ws {
   uint2* rec_rect;           // [total_quads]: pixel AABB (px0 | px1 << 16, py0 | py1 << 16)
   uint32_t* rec_info;        // [total_quads]: kInfo* bits | cull reason << 8
   float* rec_rep;            // [total_quads]: representative 1/w over the quad's whole box
+  float2* rec_inv;           // [total_quads]: 1 / (float)|doubled area| of triangles 0 and 1
   uint32_t* bin_count;       // [total_bins]
   uint32_t* bin_off;         // [total_bins + 1]
   uint32_t* bin_cursor;      // [total_bins]

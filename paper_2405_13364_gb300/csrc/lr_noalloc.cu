@@ -98,6 +98,7 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
   const size_t o_rect = o; o = up256(o + 8 * (size_t)Q);
   const size_t o_info = o; o = up256(o + 4 * (size_t)Q);
   const size_t o_rep = o; o = up256(o + 4 * (size_t)Q);
+  const size_t o_inv = o; o = up256(o + 8 * (size_t)Q);
   const size_t o_cnt = o; o = up256(o + 4 * (size_t)nbins);
   const size_t o_off = o; o = up256(o + 4 * ((size_t)nbins + 1));
   const size_t o_cur = o; o = up256(o + 4 * (size_t)nbins);
@@ -181,6 +182,7 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
   ws.rec_rect = reinterpret_cast<uint2*>(base + o_rect);
   ws.rec_info = reinterpret_cast<uint32_t*>(base + o_info);
   ws.rec_rep = reinterpret_cast<float*>(base + o_rep);
+  ws.rec_inv = reinterpret_cast<float2*>(base + o_inv);
   ws.bin_count = reinterpret_cast<uint32_t*>(base + o_cnt);
   ws.bin_off = reinterpret_cast<uint32_t*>(base + o_off);
   ws.bin_cursor = reinterpret_cast<uint32_t*>(base + o_cur);

@@ -78,7 +78,7 @@ __device__ __forceinline__ void edges64(const TriSm& T, int px, int py, long lon
 
 // Builds the per-half-block record of triangle t of a quad; returns false if the triangle
 // has zero area or its pixel AABB misses the half-block.
-__device__ __forceinline__ bool setup_tri(TriSm& T, const int X[4], const int Y[4], const float qv[4],
+static __device__ __noinline__ bool setup_tri(TriSm& T, const int X[4], const int Y[4], const float qv[4],
                                           uint32_t info, int t, uint32_t jl, int ox, int oy,
                                           int cor[3], int box[4], int le[3], int lsx[3], int lsy[3]) {
   if (!(info & (t ? kInfoTri1 : kInfoTri0))) return false;
@@ -129,6 +129,51 @@ __device__ __forceinline__ bool setup_tri(TriSm& T, const int X[4], const int Y[
     if (!owned) flags |= 1u << (3 + k);
   }
   if (fast) flags |= kTriFast;
+  T.ea = make_int4(le[1], le[2], lsx[1], lsx[2]);
+  T.eb = make_int4(lsy[1], lsy[2], (int)flags, (int)(2u * jl + (uint32_t)t));
+  return true;
+}
+
+// setup_tri for a triangle that k_setup marked small (kInfoSmall0 << t): the orientation
+// and 1/area come precomputed, and every edge value on a half-block the triangle's box
+// touches fits in 32 bits, so the whole set-up is 32-bit integer arithmetic.
+__device__ __forceinline__ bool setup_tri_small(TriSm& T, const int X[4], const int Y[4], const float qv[4],
+                                                float inv, uint32_t info, int t, uint32_t jl, int ox, int oy,
+                                                int cor[3], int box[4], int le[3], int lsx[3], int lsy[3]) {
+  if (!(info & (t ? kInfoTri1 : kInfoTri0))) return false;
+  int xa = X[0], ya = Y[0];
+  int xb = t ? X[2] : X[1], yb = t ? Y[2] : Y[1];
+  int xc = t ? X[3] : X[2], yc = t ? Y[3] : Y[2];
+  float qa = qv[0], qb = t ? qv[2] : qv[1], qc = t ? qv[3] : qv[2];
+  int ib = t ? 2 : 1, ic = t ? 3 : 2;
+  if (info & (kInfoSwap0 << t)) {
+    int ti = xb; xb = xc; xc = ti;
+    ti = yb; yb = yc; yc = ti;
+    const float tq = qb; qb = qc; qc = tq;
+    ti = ib; ib = ic; ic = ti;
+  }
+  // pixel-centre box: ceil((min - 128) / 256) .. floor((max - 128) / 256)
+  const int bx0 = (min(xa, min(xb, xc)) + 127) >> 8, bx1 = (max(xa, max(xb, xc)) - 128) >> 8;
+  const int by0 = (min(ya, min(yb, yc)) + 127) >> 8, by1 = (max(ya, max(yb, yc)) - 128) >> 8;
+  if (bx0 > ox + kHbW - 1 || bx1 < ox || by0 > oy + kHbH - 1 || by1 < oy) return false;
+  box[0] = max(bx0 - ox, 0);
+  box[1] = min(bx1 - ox, kHbW - 1);
+  box[2] = max(by0 - oy, 0);
+  box[3] = min(by1 - oy, kHbH - 1);
+  cor[0] = 0; cor[1] = ib; cor[2] = ic;
+  T.kq = make_float4(qa, __fsub_rn(qb, qa), __fsub_rn(qc, qa), inv);
+  uint32_t flags = kTriValid | kTriFast;
+  const int P0x = 256 * ox + 128, P0y = 256 * oy + 128;
+  const int ux[3] = {xb, xc, xa}, uy[3] = {yb, yc, ya}, wx[3] = {xc, xa, xb}, wy[3] = {yc, ya, yb};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int dx = wx[k] - ux[k], dy = wy[k] - uy[k];
+    const bool owned = dy < 0 || (dy == 0 && dx > 0);
+    le[k] = (int)((uint32_t)dx * (uint32_t)(P0y - uy[k]) - (uint32_t)dy * (uint32_t)(P0x - ux[k])) - (owned ? 0 : 1);
+    lsx[k] = -256 * dy;
+    lsy[k] = 256 * dx;
+    if (!owned) flags |= 1u << (3 + k);
+  }
   T.ea = make_int4(le[1], le[2], lsx[1], lsx[2]);
   T.eb = make_int4(lsy[1], lsy[2], (int)flags, (int)(2u * jl + (uint32_t)t));
   return true;
@@ -367,6 +412,7 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
         const int4 A = ws.rec_xy[2ull * rec], B = ws.rec_xy[2ull * rec + 1];
         const float4 Qv = ws.rec_q[rec];
         const uint32_t info = ws.rec_info[rec];
+        const float2 iv = ws.rec_inv[rec];
         const int X[4] = {A.x, A.z, B.x, B.z}, Y[4] = {A.y, A.w, B.y, B.w};
         const float qv[4] = {Qv.x, Qv.y, Qv.z, Qv.w};
         const uint32_t jl = (uint32_t)(rec - V.quad_base);
@@ -374,7 +420,10 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
         for (int t = 0; t < 2; ++t) {
           TriSm& T = tris[2 * lane + t];
           int cor[3], box[4], le[3], lsx[3], lsy[3];
-          if (!setup_tri(T, X, Y, qv, info, t, jl, ox, oy, cor, box, le, lsx, lsy)) continue;
+          const bool ok = (info & (kInfoSmall0 << t))
+                              ? setup_tri_small(T, X, Y, qv, t ? iv.y : iv.x, info, t, jl, ox, oy, cor, box, le, lsx, lsy)
+                              : setup_tri(T, X, Y, qv, info, t, jl, ox, oy, cor, box, le, lsx, lsy);
+          if (!ok) continue;
           const uint32_t mk = ((uint32_t)T.eb.z & kTriFast) ? tri_mask_fast(le, lsx, lsy, box)
                                                             : tri_mask_slow(T, ox, oy, box);
           if (t == 0) tm0 = mk; else tm1 = mk;

@@ -100,6 +100,7 @@ __global__ __launch_bounds__(256) void k_setup(Ws ws) {
     }
     uint32_t info = 0;
     float rep = 0.f;
+    float2 inv = make_float2(0.f, 0.f);
     uint2 rect = make_uint2(kRectInvisible, kRectInvisible);
     if (worst == kVisible) {
       const long long a0 = area2(X[0], Y[0], X[1], Y[1], X[2], Y[2]);
@@ -108,6 +109,26 @@ __global__ __launch_bounds__(256) void k_setup(Ws ws) {
         worst = kDegenerate;
       } else {
         info |= (a0 != 0 ? kInfoTri0 : 0u) | (a1 != 0 ? kInfoTri1 : 0u);
+        // per-triangle constants that every half-block would otherwise recompute: the
+        // orientation, 1/area of the depth interpolation (Sec. 2, "Stage 3"), and whether
+        // 32-bit edge arithmetic is exact wherever the triangle is rasterised. A half-block
+        // touching the triangle's pixel box holds pixel centres within 7 px (x) and 3 px (y)
+        // of the vertex box, so |E| <= Wx (Wy + 3*256) + Wy (Wx + 7*256) + 1 there.
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          long long A = t ? a1 : a0;
+          if (A == 0) continue;
+          if (A < 0) {
+            info |= kInfoSwap0 << t;
+            A = -A;
+          }
+          const float it = __fdiv_rn(1.0f, __ll2float_rn(A));
+          if (t) inv.y = it; else inv.x = it;
+          const int xb = t ? X[2] : X[1], yb = t ? Y[2] : Y[1], xc = t ? X[3] : X[2], yc = t ? Y[3] : Y[2];
+          const long long wx = (long long)max(X[0], max(xb, xc)) - min(X[0], min(xb, xc));
+          const long long wy = (long long)max(Y[0], max(yb, yc)) - min(Y[0], min(yb, yc));
+          if (wx * (wy + 3 * 256) + wy * (wx + 7 * 256) + 1 < (1LL << 30)) info |= kInfoSmall0 << t;
+        }
         const int xmin = min(min(X[0], X[1]), min(X[2], X[3]));
         const int xmax = max(max(X[0], X[1]), max(X[2], X[3]));
         const int ymin = min(min(Y[0], Y[1]), min(Y[2], Y[3]));
@@ -139,6 +160,7 @@ __global__ __launch_bounds__(256) void k_setup(Ws ws) {
     ws.rec_rect[g] = rect;
     ws.rec_info[g] = info | (worst << 8);
     ws.rec_rep[g] = rep;
+    ws.rec_inv[g] = inv;
     if (bad) set_error(ws.ctrl, LR_ERR_INVALID_ARG);
   }
   // per-warp statistics: one atomic per reason present in the warp
