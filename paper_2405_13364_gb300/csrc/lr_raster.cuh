@@ -34,6 +34,9 @@
 namespace lr {
 
 constexpr uint32_t kTriValid = 1u, kTriFast = 2u, kTriFlatCol = 4u;   // + corr bits 3..5
+// all three vertices at the same 1/w: the depth key is q0 at every pixel (the
+// interpolation adds l1 * 0 + l2 * 0 with l1, l2 >= 0)
+constexpr uint32_t kTriConstKey = 64u;
 constexpr unsigned long long kSent = ~0ull;
 constexpr int kRasterThreads = 256;
 #ifndef LR_RASTER_MIN_BLOCKS
@@ -109,7 +112,7 @@ static __device__ __noinline__ bool setup_tri(TriSm& T, const int X[4], const in
   T.X[0] = xa; T.X[1] = xb; T.X[2] = xc;
   T.Y[0] = ya; T.Y[1] = yb; T.Y[2] = yc;
   T.kq = make_float4(qa, __fsub_rn(qb, qa), __fsub_rn(qc, qa), __fdiv_rn(1.0f, __ll2float_rn(A)));
-  uint32_t flags = kTriValid;
+  uint32_t flags = kTriValid | ((qb == qa && qc == qa) ? kTriConstKey : 0u);
   bool fast = true;
   const long long P0x = 256LL * ox + 128, P0y = 256LL * oy + 128;
   const long long lim = 1LL << 30;
@@ -162,7 +165,7 @@ __device__ __forceinline__ bool setup_tri_small(TriSm& T, const int X[4], const 
   box[3] = min(by1 - oy, kHbH - 1);
   cor[0] = 0; cor[1] = ib; cor[2] = ic;
   T.kq = make_float4(qa, __fsub_rn(qb, qa), __fsub_rn(qc, qa), inv);
-  uint32_t flags = kTriValid | kTriFast;
+  uint32_t flags = kTriValid | kTriFast | ((qb == qa && qc == qa) ? kTriConstKey : 0u);
   const int P0x = 256 * ox + 128, P0y = 256 * oy + 128;
   const int ux[3] = {xb, xc, xa}, uy[3] = {yb, yc, ya}, wx[3] = {xc, xa, xb}, wy[3] = {yc, ya, yb};
 #pragma unroll
@@ -270,8 +273,11 @@ __device__ __forceinline__ float tri_key(const TriSm& T, int4 ea, int4 eb, float
 
 template <int K, bool VTX, bool BWD = false>
 struct PixelState {
+  // K = 1 with flat colours gathered at blend time: the colour of the fragment held in the
+  // slot is loaded when it enters, so the gather overlaps the next fragment's work
+  static constexpr bool kPrefetch = !VTX && K == 1;
   unsigned long long s[K];
-  float4 c[VTX ? K : 1];
+  float4 c[VTX || kPrefetch ? K : 1];
   unsigned long long last;
   float r, g, b, T;
   bool flagged;
@@ -288,7 +294,7 @@ struct PixelState {
 
   __device__ __forceinline__ void blend(unsigned long long key, float4 col, const ViewDev& V) {
     const uint32_t j = (uint32_t)key >> 1;
-    if (!VTX) col = __ldg(reinterpret_cast<const float4*>(V.col) + j);
+    if (!VTX && !kPrefetch) col = __ldg(reinterpret_cast<const float4*>(V.col) + j);
     const float w = T * col.w;
     r += w * col.x;
     g += w * col.y;
@@ -313,6 +319,21 @@ struct PixelState {
   __device__ __forceinline__ void insert(unsigned long long x, float4 xc, const ViewDev& V) {
     if (x > last) {   // nearer than a fragment already blended: order not guaranteed
       flagged = true;
+      return;
+    }
+    if (kPrefetch) {
+      const float4* cp = reinterpret_cast<const float4*>(V.col) + ((uint32_t)x >> 1);
+      if (x > s[0]) {          // nearer than the held fragment: blend it at once
+        blend(x, __ldg(cp), V);
+        last = x;
+      } else {
+        if (s[0] != kSent) {
+          blend(s[0], c[0], V);
+          last = s[0];
+        }
+        s[0] = x;
+        c[0] = __ldg(cp);
+      }
       return;
     }
     const bool xfirst = x > s[0];
@@ -344,7 +365,7 @@ struct PixelState {
   __device__ __forceinline__ void flush(const ViewDev& V) {
 #pragma unroll
     for (int i = 0; i < K; ++i)
-      if (s[i] != kSent) blend(s[i], VTX ? c[i] : make_float4(0.f, 0.f, 0.f, 0.f), V);
+      if (s[i] != kSent) blend(s[i], VTX || kPrefetch ? c[i] : make_float4(0.f, 0.f, 0.f, 0.f), V);
   }
 };
 
@@ -465,8 +486,9 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
           const int4 ea = T.ea, eb = T.eb;
           const float4 kq = T.kq;
           const uint32_t fl = (uint32_t)eb.z, id = (uint32_t)eb.w;
-          float l1, l2;
-          const float key = tri_key(T, ea, eb, kq, lx, ly, px, py, l1, l2);
+          float l1 = 0.f, l2 = 0.f;
+          // (the colour-carrying variant keeps one path: its branch cost more than it saved)
+          const float key = (!VTX && (fl & kTriConstKey)) ? kq.x : tri_key(T, ea, eb, kq, lx, ly, px, py, l1, l2);
           const unsigned long long sk = ((unsigned long long)__float_as_uint(key) << 32) | id;
           ++cnt;
           if (V.hash) hsh += splitmix64(id);
