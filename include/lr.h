@@ -129,18 +129,22 @@ typedef struct {
 /* Byte offsets, inside a workspace, of the per-quad records written by the setup stage and
  * of the binning arrays (for tests and inspection; valid after the render's stream has
  * finished and until the workspace is reused):
- *   rec_xy    i32[Q][8]  snapped vertex positions X0 Y0 X1 Y1 X2 Y2 X3 Y3 (1/256 pixel)
- *   rec_q     f32[Q][4]  1/w of each vertex
+ *   rec       u32[Q][16] per quad: X0 Y0 X1 Y1 X2 Y2 X3 Y3 (snapped, 1/256 pixel), the
+ *                        four vertices' 1/w (f32 bits), 1/|A0| and 1/|A1| (f32 bits of the
+ *                        reciprocal doubled triangle areas, 0 for a zero-area triangle),
+ *                        info (as rec_info), 0
  *   rec_rect  u32[Q][2]  pixel-centre AABB: px0 | px1 << 16, py0 | py1 << 16
  *                        (0x0000FFFF, 0x0000FFFF for a culled quad)
  *   rec_info  u32[Q]     bit 0/1: triangle 0/1 has non-zero area, bit 2: spans more than
- *                        4x4 bins, bit 3: all vertices at the same 1/w, bits 8..11: cull
- *                        reason (0 = visible)
+ *                        4x4 bins, bit 3: all vertices at the same 1/w, bits 4/5: triangle
+ *                        0/1 has negative area (v1, v2 swapped), bits 6/7: triangle 0/1 is
+ *                        small enough for 32-bit edge arithmetic, bits 8..11: cull reason
+ *                        (0 = visible)
  *   bin_off   u32[bins+1] start of each bin's reference list in refs
  *   refs      u64[capacity] per-bin reference lists, sorted front to back
  * Quads, bins and pixels of a batch are numbered view after view. */
 typedef struct {
-  size_t rec_xy, rec_q, rec_rect, rec_info, bin_count, bin_off, refs;
+  size_t rec, rec_rect, rec_info, bin_count, bin_off, refs;
   int64_t total_quads, total_bins, refs_capacity;
 } lr_ws_layout;
 

@@ -77,7 +77,7 @@ class lr_stats(ctypes.Structure):
 
 
 class lr_ws_layout(ctypes.Structure):
-    _fields_ = [("rec_xy", ctypes.c_size_t), ("rec_q", ctypes.c_size_t), ("rec_rect", ctypes.c_size_t),
+    _fields_ = [("rec", ctypes.c_size_t), ("rec_rect", ctypes.c_size_t),
                 ("rec_info", ctypes.c_size_t), ("bin_count", ctypes.c_size_t),
                 ("bin_off", ctypes.c_size_t), ("refs", ctypes.c_size_t),
                 ("total_quads", ctypes.c_int64), ("total_bins", ctypes.c_int64),

@@ -74,7 +74,7 @@ static const RasterVariant kVariants[] = {
 };
 
 struct Layout {
-  size_t ctrl, views, rec_xy, rec_q, rec_rect, rec_info, rec_rep, rec_inv, bin_count, bin_off, bin_cursor, bin_order;
+  size_t ctrl, views, rec, rec_rect, rec_info, rec_rep, bin_count, bin_off, bin_cursor, bin_order;
   size_t refs, refs_tmp, ref_hb, ovf_list, total;
   long long total_quads = 0, total_pix = 0, refs_cap = 0;
   int total_bins = 0, total_chunks = 0;
@@ -98,12 +98,10 @@ static Layout make_layout(int n, const long long* Q, const int* W, const int* H)
   auto take = [&](size_t bytes) { const size_t at = o; o = align256(o + bytes); return at; };
   L.ctrl = take(sizeof(Ctrl));
   L.views = take(sizeof(ViewDev) * (size_t)n);
-  L.rec_xy = take(sizeof(int4) * 2 * (size_t)L.total_quads);
-  L.rec_q = take(sizeof(float4) * (size_t)L.total_quads);
+  L.rec = take(sizeof(int4) * 4 * (size_t)L.total_quads);
   L.rec_rect = take(sizeof(uint2) * (size_t)L.total_quads);
   L.rec_info = take(sizeof(uint32_t) * (size_t)L.total_quads);
   L.rec_rep = take(sizeof(float) * (size_t)L.total_quads);
-  L.rec_inv = take(sizeof(float2) * (size_t)L.total_quads);
   L.bin_count = take(sizeof(uint32_t) * (size_t)L.total_bins);
   L.bin_off = take(sizeof(uint32_t) * ((size_t)L.total_bins + 1));
   L.bin_cursor = take(sizeof(uint32_t) * (size_t)L.total_bins);
@@ -152,12 +150,10 @@ static Ws make_ws(const Layout& L, void* base, int n_views) {
   w.total_quads = L.total_quads;
   w.total_pix = L.total_pix;
   w.refs_cap = L.refs_cap;
-  w.rec_xy = reinterpret_cast<int4*>(b + L.rec_xy);
-  w.rec_q = reinterpret_cast<float4*>(b + L.rec_q);
+  w.rec = reinterpret_cast<int4*>(b + L.rec);
   w.rec_rect = reinterpret_cast<uint2*>(b + L.rec_rect);
   w.rec_info = reinterpret_cast<uint32_t*>(b + L.rec_info);
   w.rec_rep = reinterpret_cast<float*>(b + L.rec_rep);
-  w.rec_inv = reinterpret_cast<float2*>(b + L.rec_inv);
   w.bin_count = reinterpret_cast<uint32_t*>(b + L.bin_count);
   w.bin_off = reinterpret_cast<uint32_t*>(b + L.bin_off);
   w.bin_cursor = reinterpret_cast<uint32_t*>(b + L.bin_cursor);
@@ -350,8 +346,7 @@ extern "C" lr_status lr_workspace_layout(const lr_ctx* ctx, int32_t n_views, con
   lr_status s = layout_for(const_cast<lr_ctx*>(ctx), n_views, views, &L);
   if (s != LR_OK) return s;
   set_capacity(L, workspace_bytes);
-  out->rec_xy = L.rec_xy;
-  out->rec_q = L.rec_q;
+  out->rec = L.rec;
   out->rec_rect = L.rec_rect;
   out->rec_info = L.rec_info;
   out->bin_count = L.bin_count;

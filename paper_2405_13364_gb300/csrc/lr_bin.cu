@@ -66,7 +66,7 @@ __device__ bool tri_may_touch_bin(const int X[4], const int Y[4], int t, int bx,
 
 __device__ __forceinline__ bool quad_may_touch_bin(const Ws& ws, long long q, uint32_t info, int bx,
                                                    int by, int W, int H) {
-  const int4 a = ws.rec_xy[2 * q], b = ws.rec_xy[2 * q + 1];
+  const int4 a = ws.rec[4 * q], b = ws.rec[4 * q + 1];
   const int X[4] = {a.x, a.z, b.x, b.z}, Y[4] = {a.y, a.w, b.y, b.w};
   return ((info & kInfoTri0) && tri_may_touch_bin(X, Y, 0, bx, by, W, H)) ||
          ((info & kInfoTri1) && tri_may_touch_bin(X, Y, 1, bx, by, W, H));
@@ -75,10 +75,9 @@ __device__ __forceinline__ bool quad_may_touch_bin(const Ws& ws, long long q, ui
 // Per-bin representative depth of a quad that spans several bins.
 __device__ __forceinline__ float rep_depth(const Ws& ws, long long q, uint32_t info, int x0, int x1,
                                            int y0, int y1) {
-  const int4 a = ws.rec_xy[2 * q], b = ws.rec_xy[2 * q + 1];
-  const float4 qq = ws.rec_q[q];
+  const int4 a = ws.rec[4 * q], b = ws.rec[4 * q + 1], c = ws.rec[4 * q + 2];
   const int X[4] = {a.x, a.z, b.x, b.z}, Y[4] = {a.y, a.w, b.y, b.w};
-  const float Q[4] = {qq.x, qq.y, qq.z, qq.w};
+  const float Q[4] = {__int_as_float(c.x), __int_as_float(c.y), __int_as_float(c.z), __int_as_float(c.w)};
   return rep_depth_of(X, Y, Q, info, x0, x1, y0, y1);
 }
 

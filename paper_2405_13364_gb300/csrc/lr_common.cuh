@@ -84,6 +84,31 @@ struct Ctrl {
   unsigned long long pad[8];
 };
 
+// The per-quad record written by k_setup and gathered by every later stage, 64 bytes so
+// that one quad is four 16-byte loads from one cache line:
+//   w0 = (X0, Y0, X1, Y1), w1 = (X2, Y2, X3, Y3)  snapped vertices, 1/256 pixel
+//   w2 = 1/w of vertices 0..3 (float bits)
+//   w3 = (1 / (float)|A0|, 1 / (float)|A1| (float bits, 0 for a zero-area triangle), info, 0)
+struct QuadRec {
+  int X[4], Y[4];
+  float q[4];
+  float inv[2];
+  uint32_t info;
+};
+
+__device__ __forceinline__ QuadRec load_rec(const int4* rec, uint32_t i) {
+  const int4* p = rec + 4ull * i;
+  const int4 a = p[0], b = p[1], c = p[2], d = p[3];
+  QuadRec r;
+  r.X[0] = a.x; r.Y[0] = a.y; r.X[1] = a.z; r.Y[1] = a.w;
+  r.X[2] = b.x; r.Y[2] = b.y; r.X[3] = b.z; r.Y[3] = b.w;
+  r.q[0] = __int_as_float(c.x); r.q[1] = __int_as_float(c.y);
+  r.q[2] = __int_as_float(c.z); r.q[3] = __int_as_float(c.w);
+  r.inv[0] = __int_as_float(d.x); r.inv[1] = __int_as_float(d.y);
+  r.info = (uint32_t)d.z;
+  return r;
+}
+
 // Pointers into the workspace for one render (passed by value to every kernel).
 struct Ws {
   Ctrl* ctrl;
@@ -93,12 +118,10 @@ struct Ws {
   long long total_quads;
   long long total_pix;
   long long refs_cap;
-  int4* rec_xy;              // [2 * total_quads]: (X0,Y0,X1,Y1), (X2,Y2,X3,Y3) 8-bit subpixel
-  float4* rec_q;             // [total_quads]: 1/w per vertex
+  int4* rec;                 // [4 * total_quads]: the 64-byte quad record (QuadRec)
   uint2* rec_rect;           // [total_quads]: pixel AABB (px0 | px1 << 16, py0 | py1 << 16)
   uint32_t* rec_info;        // [total_quads]: kInfo* bits | cull reason << 8
   float* rec_rep;            // [total_quads]: representative 1/w over the quad's whole box
-  float2* rec_inv;           // [total_quads]: 1 / (float)|doubled area| of triangles 0 and 1
   uint32_t* bin_count;       // [total_bins]
   uint32_t* bin_off;         // [total_bins + 1]
   uint32_t* bin_cursor;      // [total_bins]

@@ -93,12 +93,11 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
   size_t o = 0;
   const size_t o_ctrl = o; o = up256(o + sizeof(Ctrl));
   const size_t o_view = o; o = up256(o + sizeof(ViewDev));
-  const size_t o_xy = o; o = up256(o + 32 * (size_t)Q);
-  const size_t o_q = o; o = up256(o + 16 * (size_t)Q);
+  const bool vtx = q.color_mode == LR_COLOR_VERTEX;
+  const size_t o_rec = o; o = up256(o + 64 * (size_t)Q);
   const size_t o_rect = o; o = up256(o + 8 * (size_t)Q);
   const size_t o_info = o; o = up256(o + 4 * (size_t)Q);
   const size_t o_rep = o; o = up256(o + 4 * (size_t)Q);
-  const size_t o_inv = o; o = up256(o + 8 * (size_t)Q);
   const size_t o_cnt = o; o = up256(o + 4 * (size_t)nbins);
   const size_t o_off = o; o = up256(o + 4 * ((size_t)nbins + 1));
   const size_t o_cur = o; o = up256(o + 4 * (size_t)nbins);
@@ -177,12 +176,10 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
   ws.total_quads = Q;
   ws.total_pix = npix;
   ws.refs_cap = cap;
-  ws.rec_xy = reinterpret_cast<int4*>(base + o_xy);
-  ws.rec_q = reinterpret_cast<float4*>(base + o_q);
+  ws.rec = reinterpret_cast<int4*>(base + o_rec);
   ws.rec_rect = reinterpret_cast<uint2*>(base + o_rect);
   ws.rec_info = reinterpret_cast<uint32_t*>(base + o_info);
   ws.rec_rep = reinterpret_cast<float*>(base + o_rep);
-  ws.rec_inv = reinterpret_cast<float2*>(base + o_inv);
   ws.bin_count = reinterpret_cast<uint32_t*>(base + o_cnt);
   ws.bin_off = reinterpret_cast<uint32_t*>(base + o_off);
   ws.bin_cursor = reinterpret_cast<uint32_t*>(base + o_cur);
@@ -203,8 +200,8 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
   if (chunks > 0) k_bin_scatter<<<chunks, kBinThreads, 0, st>>>(ws);
   k_bin_sort<<<(int)nbins, 256, kSortSmemCap * sizeof(unsigned long long), st>>>(ws);
   k_bin_sort_big<<<ds.sms, kSortBigThreads, 2 * kSortBigCap * sizeof(unsigned long long), st>>>(ws);
-  const bool vtx = Q > 0 && q.color_mode == LR_COLOR_VERTEX;
-  if (launch_raster_3(vtx ? 1 : 0, ws, ds.sms * (vtx ? ds.blocks_vtx : ds.blocks_flat), st) != cudaSuccess)
+  const bool vtx_kernel = Q > 0 && vtx;
+  if (launch_raster_3(vtx_kernel ? 1 : 0, ws, ds.sms * (vtx_kernel ? ds.blocks_vtx : ds.blocks_flat), st) != cudaSuccess)
     return LR_ERR_CUDA;
   if (launch_overflow(false, ws, ds.sms * ds.ovf_blocks, st) != cudaSuccess) return LR_ERR_CUDA;
   if (device_status) k_noalloc_status<<<1, 1, 0, st>>>(ws.ctrl, device_status);

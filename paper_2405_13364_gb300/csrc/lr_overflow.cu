@@ -22,15 +22,10 @@ namespace lr {
 // centre is not covered; otherwise the sort key and straight RGBA colour.
 __device__ bool frag_eval(const Ws& ws, const ViewDev& V, uint32_t rec, int t, int px, int py,
                           unsigned long long* sk, float4* col) {
-  const uint32_t info = ws.rec_info[rec];
-  if (!(info & (t ? kInfoTri1 : kInfoTri0))) return false;
-  const int4 A4 = ws.rec_xy[2ull * rec], B4 = ws.rec_xy[2ull * rec + 1];
-  const int X[4] = {A4.x, A4.z, B4.x, B4.z}, Y[4] = {A4.y, A4.w, B4.y, B4.w};
-  const float4 Qv = ws.rec_q[rec];
-  const float qv[4] = {Qv.x, Qv.y, Qv.z, Qv.w};
+  const QuadRec R = load_rec(ws.rec, rec);
+  if (!(R.info & (t ? kInfoTri1 : kInfoTri0))) return false;
   int ia = 0, ib = t ? 2 : 1, ic = t ? 3 : 2;
-  long long A = area2(X[ia], Y[ia], X[ib], Y[ib], X[ic], Y[ic]);
-  if (A < 0) { const int tmp = ib; ib = ic; ic = tmp; A = -A; }
+  if (R.info & (kInfoSwap0 << t)) { const int tmp = ib; ib = ic; ic = tmp; }
   const int vi[3] = {ia, ib, ic};
   const long long Px = 256LL * px + 128, Py = 256LL * py + 128;
   long long e[3];
@@ -38,22 +33,23 @@ __device__ bool frag_eval(const Ws& ws, const ViewDev& V, uint32_t rec, int t, i
   for (int k = 0; k < 3; ++k) {
     const int u = vi[k == 0 ? 1 : (k == 1 ? 2 : 0)];
     const int w = vi[k == 0 ? 2 : (k == 1 ? 0 : 1)];
-    const long long dx = (long long)X[w] - X[u], dy = (long long)Y[w] - Y[u];
-    e[k] = dx * (Py - Y[u]) - dy * (Px - X[u]);
+    const long long dx = (long long)R.X[w] - R.X[u], dy = (long long)R.Y[w] - R.Y[u];
+    e[k] = dx * (Py - R.Y[u]) - dy * (Px - R.X[u]);
     const bool owned = dy < 0 || (dy == 0 && dx > 0);
     if (!(e[k] > 0 || (e[k] == 0 && owned))) return false;
   }
-  const float inv = __fdiv_rn(1.0f, __ll2float_rn(A));
+  const float inv = R.inv[t];
   const float l1 = __fmul_rn(__ll2float_rn(e[1]), inv);
   const float l2 = __fmul_rn(__ll2float_rn(e[2]), inv);
-  const float key = __fadd_rn(qv[ia], __fadd_rn(__fmul_rn(l1, __fsub_rn(qv[ib], qv[ia])),
-                                                 __fmul_rn(l2, __fsub_rn(qv[ic], qv[ia]))));
+  const float key = __fadd_rn(R.q[ia], __fadd_rn(__fmul_rn(l1, __fsub_rn(R.q[ib], R.q[ia])),
+                                                  __fmul_rn(l2, __fsub_rn(R.q[ic], R.q[ia]))));
   const uint32_t jl = (uint32_t)(rec - V.quad_base);
   *sk = ((unsigned long long)__float_as_uint(key) << 32) | (2u * jl + (uint32_t)t);
   if (col) {
     if (V.color_mode == LR_COLOR_FLAT) {
       *col = __ldg(reinterpret_cast<const float4*>(V.col) + jl);
     } else {
+      // perspective-correct: sum_k (l_k q_k) c_k / sum_k l_k q_k
       uint4 q4;
       if (V.idx) q4 = __ldg(reinterpret_cast<const uint4*>(V.idx) + jl);
       else q4 = make_uint4(4 * jl, 4 * jl + 1, 4 * jl + 2, 4 * jl + 3);
@@ -64,7 +60,7 @@ __device__ bool frag_eval(const Ws& ws, const ViewDev& V, uint32_t rec, int t, i
       float den = 0.f;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const float wk = ls[k] * qv[vi[k]];
+        const float wk = ls[k] * R.q[vi[k]];
         const float4 c = __ldg(reinterpret_cast<const float4*>(V.col) + vids[vi[k]]);
         num.x += wk * c.x; num.y += wk * c.y; num.z += wk * c.z; num.w += wk * c.w;
         den += wk;

@@ -246,6 +246,13 @@ static __device__ __noinline__ uint32_t tri_mask_slow(const TriSm& T, int ox, in
   return mask;
 }
 
+// Approximate reciprocal (PTX rcp.approx.ftz.f32, about 1 ulp), for colours only.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // Exact depth key (interpolated 1/w, Sec. 2 "Stage 3", the reading O.8 of the depth
 // formula) of a triangle record at pixel (px, py) = (ox + lx, oy + ly) of its half-block;
 // also returns the barycentric weights l1, l2 it used.
@@ -425,25 +432,21 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
     uint32_t cnt = 0;
     unsigned long long hsh = 0;
 
-    auto process = [&](int nc, uint32_t ref) {
+    auto process = [&](int nc, uint32_t rec) {
       // ---- 2. triangle setup and coverage masks, one quad per lane ---------------------
       uint32_t tm0 = 0, tm1 = 0;
       if (lane < nc) {
-        const uint32_t rec = ~(uint32_t)ws.refs[off + ref];
-        const int4 A = ws.rec_xy[2ull * rec], B = ws.rec_xy[2ull * rec + 1];
-        const float4 Qv = ws.rec_q[rec];
-        const uint32_t info = ws.rec_info[rec];
-        const float2 iv = ws.rec_inv[rec];
-        const int X[4] = {A.x, A.z, B.x, B.z}, Y[4] = {A.y, A.w, B.y, B.w};
-        const float qv[4] = {Qv.x, Qv.y, Qv.z, Qv.w};
+        const QuadRec R = load_rec(ws.rec, rec);
         const uint32_t jl = (uint32_t)(rec - V.quad_base);
+        uint4 vi = make_uint4(4 * jl, 4 * jl + 1, 4 * jl + 2, 4 * jl + 3);
+        if (VTX && vtx_view && V.idx) vi = __ldg(reinterpret_cast<const uint4*>(V.idx) + jl);
 #pragma unroll 1
         for (int t = 0; t < 2; ++t) {
           TriSm& T = tris[2 * lane + t];
           int cor[3], box[4], le[3], lsx[3], lsy[3];
-          const bool ok = (info & (kInfoSmall0 << t))
-                              ? setup_tri_small(T, X, Y, qv, t ? iv.y : iv.x, info, t, jl, ox, oy, cor, box, le, lsx, lsy)
-                              : setup_tri(T, X, Y, qv, info, t, jl, ox, oy, cor, box, le, lsx, lsy);
+          const bool ok = (R.info & (kInfoSmall0 << t))
+                              ? setup_tri_small(T, R.X, R.Y, R.q, R.inv[t], R.info, t, jl, ox, oy, cor, box, le, lsx, lsy)
+                              : setup_tri(T, R.X, R.Y, R.q, R.info, t, jl, ox, oy, cor, box, le, lsx, lsy);
           if (!ok) continue;
           const uint32_t mk = ((uint32_t)T.eb.z & kTriFast) ? tri_mask_fast(le, lsx, lsy, box)
                                                             : tri_mask_slow(T, ox, oy, box);
@@ -454,17 +457,21 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
               qc[0] = __ldg(reinterpret_cast<const float4*>(V.col) + jl);
               T.eb.z |= (int)kTriFlatCol;
             } else {
-              uint4 vi;
-              if (V.idx) vi = __ldg(reinterpret_cast<const uint4*>(V.idx) + jl);
-              else vi = make_uint4(4 * jl, 4 * jl + 1, 4 * jl + 2, 4 * jl + 3);
+              // corner colours times 1/w as (c0, c1 - c0, c2 - c0) for the fragment's
+              // c0 + l1 (c1 - c0) + l2 (c2 - c0)
+              float4 a[3];
 #pragma unroll
               for (int k = 0; k < 3; ++k) {
                 const int ck = cor[k];
                 const uint32_t vid = ck == 0 ? vi.x : (ck == 1 ? vi.y : (ck == 2 ? vi.z : vi.w));
-                const float qk = ck == 0 ? qv[0] : (ck == 1 ? qv[1] : (ck == 2 ? qv[2] : qv[3]));
+                const float qk = ck == 0 ? R.q[0] : (ck == 1 ? R.q[1] : (ck == 2 ? R.q[2] : R.q[3]));
                 const float4 cc = __ldg(reinterpret_cast<const float4*>(V.col) + vid);
-                qc[k] = make_float4(qk * cc.x, qk * cc.y, qk * cc.z, qk * cc.w);
+                a[k] = make_float4(qk * cc.x, qk * cc.y, qk * cc.z, qk * cc.w);
               }
+              const float4 a0 = a[0], a1 = a[1], a2 = a[2];
+              qc[0] = a0;
+              qc[1] = make_float4(a1.x - a0.x, a1.y - a0.y, a1.z - a0.z, a1.w - a0.w);
+              qc[2] = make_float4(a2.x - a0.x, a2.y - a0.y, a2.z - a0.z, a2.w - a0.w);
             }
           }
         }
@@ -499,13 +506,14 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
             if (fl & kTriFlatCol) {
               col = qc[0];
             } else {
-              const float l0 = 1.0f - l1 - l2;
-              const float rk = __frcp_rn(key);
-              const float4 a0 = qc[0], a1 = qc[1], a2 = qc[2];
-              col.x = (l0 * a0.x + l1 * a1.x + l2 * a2.x) * rk;
-              col.y = (l0 * a0.y + l1 * a1.y + l2 * a2.y) * rk;
-              col.z = (l0 * a0.z + l1 * a1.z + l2 * a2.z) * rk;
-              col.w = (l0 * a0.w + l1 * a1.w + l2 * a2.w) * rk;
+              // perspective-correct colour: interpolated (c / w) divided by the
+              // interpolated 1/w, which is the depth key
+              const float rk = rcp_approx(key);
+              const float4 a0 = qc[0], d1 = qc[1], d2 = qc[2];
+              col.x = (a0.x + l1 * d1.x + l2 * d2.x) * rk;
+              col.y = (a0.y + l1 * d1.y + l2 * d2.y) * rk;
+              col.z = (a0.z + l1 * d1.z + l2 * d2.z) * rk;
+              col.w = (a0.w + l1 * d1.w + l2 * d2.w) * rk;
             }
           }
           st.insert(sk, col, V);
@@ -529,12 +537,13 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
     // ---- 1. the half-block's candidates: set bits of its bitmap row, in sorted order ----
     const uint32_t* row = hb_row(ws, off, bin_g, n, hb);
     const int nw = (n + 31) >> 5;
+    const uint32_t* ref_lo = reinterpret_cast<const uint32_t*>(ws.refs + off);   // low words
     for (int g = 0; g < nw; g += 32) {
       BitRounds br;
       br.prepare(g + lane < nw ? __ldg(row + g + lane) : 0u, lane);
       for (int r0 = 0; r0 < br.total; r0 += 32) {
         const int j = br.get(r0, lane);
-        process(min(32, br.total - r0), j < 0 ? 0u : (uint32_t)(32 * g + j));
+        process(min(32, br.total - r0), j < 0 ? 0u : ~ref_lo[2 * (32 * g + j)]);
       }
     }
     if (pass == 0) pre_flagged = st.flagged;

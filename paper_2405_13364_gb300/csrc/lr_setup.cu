@@ -154,13 +154,14 @@ __global__ __launch_bounds__(256) void k_setup(Ws ws) {
       rect = make_uint2(kRectInvisible, kRectInvisible);
     }
     reason = worst;
-    ws.rec_xy[2 * g] = make_int4(X[0], Y[0], X[1], Y[1]);
-    ws.rec_xy[2 * g + 1] = make_int4(X[2], Y[2], X[3], Y[3]);
-    ws.rec_q[g] = make_float4(q[0], q[1], q[2], q[3]);
+    int4* rp = ws.rec + 4 * g;
+    rp[0] = make_int4(X[0], Y[0], X[1], Y[1]);
+    rp[1] = make_int4(X[2], Y[2], X[3], Y[3]);
+    rp[2] = make_int4(__float_as_int(q[0]), __float_as_int(q[1]), __float_as_int(q[2]), __float_as_int(q[3]));
+    rp[3] = make_int4(__float_as_int(inv.x), __float_as_int(inv.y), (int)(info | (worst << 8)), 0);
     ws.rec_rect[g] = rect;
     ws.rec_info[g] = info | (worst << 8);
     ws.rec_rep[g] = rep;
-    ws.rec_inv[g] = inv;
     if (bad) set_error(ws.ctrl, LR_ERR_INVALID_ARG);
   }
   // per-warp statistics: one atomic per reason present in the warp

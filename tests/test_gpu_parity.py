@@ -102,8 +102,9 @@ def test_setup_records_bit_exact(lr):
     def grab(o, nbytes, dtype):
         return ws[off + o: off + o + nbytes].cpu().numpy().view(dtype)
 
-    xy = grab(lay.rec_xy, 32 * q, np.int32).reshape(q, 8)
-    qq = grab(lay.rec_q, 16 * q, np.float32).reshape(q, 4)
+    rec = grab(lay.rec, 64 * q, np.int32).reshape(q, 16)
+    xy = rec[:, 0:8]
+    qq = rec[:, 8:12].view(np.float32)
     rect = grab(lay.rec_rect, 8 * q, np.uint32).reshape(q, 2)
     info = grab(lay.rec_info, 4 * q, np.uint32)
     os_ = oracle.setup(s)
