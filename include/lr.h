@@ -118,7 +118,7 @@ typedef struct {
   int64_t bin_refs;          /* (quad, bin) references produced by binning */
   int64_t bin_refs_capacity; /* what the workspace could hold */
   int64_t bins_nonempty;
-  int64_t bins_high;         /* bins sorted by the high-density (global-memory) path */
+  int64_t bins_high;         /* bins of 2048 or more references (sorted by the dense-bin path) */
   int64_t max_bin_refs;
   int64_t fragments;         /* covering (pixel, quad, triangle) fragments */
   int64_t overflow_pixels;   /* pixels re-done by the exact full sort */

@@ -234,9 +234,9 @@ extern "C" lr_status lr_create(const lr_config* config, lr_ctx** out_ctx) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e == cudaSuccess) e = c->variant->prepare(&c->raster_blocks_flat, &c->raster_blocks_vtx, &c->raster_blocks_bwd);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bin_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)(kSortSmemCap * sizeof(unsigned long long)));
+                                                 (int)kSortSmemBytes);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bin_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)(2 * kSortBigCap * sizeof(unsigned long long)));
+                                                 (int)kSortBigSmemBytes);
   if (e == cudaSuccess) e = overflow_occupancy(&c->ovf_blocks);
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&c->host_ctrl), sizeof(Ctrl));
   for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev[i]);
@@ -475,8 +475,8 @@ static lr_status launch_sequence(lr_ctx* ctx, const Prepared& P, cudaStream_t st
   rec(ctx, timed, 3, st);
   if (L.total_chunks > 0) k_bin_scatter<<<L.total_chunks, kBinThreads, 0, st>>>(ws);
   rec(ctx, timed, 4, st);
-  k_bin_sort<<<L.total_bins, 256, kSortSmemCap * sizeof(unsigned long long), st>>>(ws);
-  k_bin_sort_big<<<ctx->sms, kSortBigThreads, 2 * kSortBigCap * sizeof(unsigned long long), st>>>(ws);
+  k_bin_sort<<<L.total_bins, 256, kSortSmemBytes, st>>>(ws);
+  k_bin_sort_big<<<ctx->sms, kSortBigThreads, kSortBigSmemBytes, st>>>(ws);
   rec(ctx, timed, 5, st);
   const bool carry = P.any_vertex || (ctx->cfg.flags & LR_FLAG_CARRY_COLORS);
   const int mode = bwd ? 2 : (carry ? 1 : 0);

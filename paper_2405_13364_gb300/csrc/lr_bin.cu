@@ -17,14 +17,16 @@
 //                  (~representative 1/w) << 32 | ~record index.
 //   k_bin_sort     Stage-1 depth sort: sorts each bin's references ascending, i.e. front
 //                  to back by a representative depth, ties with the higher quad index
-//                  first. Bins with fewer than 4096 references: one 256-thread CTA per
+//                  first. Bins with fewer than 2048 references: one 256-thread CTA per
 //                  bin, a bitonic network on keys held in registers (exchanges through
 //                  registers, warp shuffles, or shared memory across warps).
-//   k_bin_sort_big The high-density bins (4096 references or more; the paper's "high"
-//                  category): persistent 1024-thread CTAs take them from the front
-//                  of the size-ordered bin list and merge-sort runs of up to 8192
-//                  references in shared memory; longer lists merge their runs through a
-//                  global buffer.
+//   k_bin_sort_big The high-density bins (2048 references or more; the paper's "high"
+//                  category): persistent 1024-thread CTAs take them from the front of the
+//                  size-ordered bin list. Up to 20480 references are bucket-sorted in
+//                  shared memory (about two references per bucket between the bin's depth
+//                  extremes, insertion sort per bucket); bins with a bucket over 64
+//                  references (many equal depths) or longer lists merge-sort runs of up to
+//                  8192 references in shared memory and merge them through a global buffer.
 #include "lr_common.cuh"
 
 namespace lr {
@@ -385,8 +387,126 @@ __device__ void cta_sort(unsigned long long* g, int n, unsigned long long* sbuf)
   if (per <= 1) cta_sort_regs<1>(g, n, sbuf);
   else if (per <= 2) cta_sort_regs<2>(g, n, sbuf);
   else if (per <= 4) cta_sort_regs<4>(g, n, sbuf);
-  else if (per <= 8) cta_sort_regs<8>(g, n, sbuf);
-  else cta_sort_regs<16>(g, n, sbuf);
+  else cta_sort_regs<8>(g, n, sbuf);
+}
+
+// Block-wide reduction / exclusive scan helpers over all threads of the CTA (blockDim a
+// multiple of 32, at most 1024); red holds 32 words of shared scratch.
+__device__ __forceinline__ uint32_t block_min_u32(uint32_t v, uint32_t* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  v = lane < nw ? red[lane] : 0xFFFFFFFFu;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ uint32_t block_max_u32(uint32_t v, uint32_t* red) {
+  return ~block_min_u32(~v, red);
+}
+// exclusive prefix sum of v over threads (in thread order); *total receives the sum
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* red, uint32_t* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  __syncthreads();
+  if (lane == 31) red[w] = incl;
+  __syncthreads();
+  uint32_t ws = lane < nw ? red[lane] : 0u;
+  uint32_t wincl = ws;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, wincl, o);
+    if (lane >= o) wincl += t;
+  }
+  *total = __shfl_sync(0xffffffffu, wincl, 31);
+  const uint32_t wbase = __shfl_sync(0xffffffffu, wincl - ws, w);
+  return wbase + incl - v;
+}
+
+// Ascending bucket sort of the 64-bit keys r[0, n) by the whole CTA, through shared memory
+// dst[n] and cnt[2 * NBMAX + 2] (NBMAX a power of two). Keys are bucketed by their high word,
+// linearly between its minimum and maximum over the list (monotone, so buckets come out in
+// order), each bucket is sorted by insertion by one thread, and the result is written back
+// to r. Returns false, with r unchanged, when a bucket would hold more than kMaxBucket keys
+// (many equal or clustered depths); the caller then uses a comparison sort.
+template <int NBMAX>
+__device__ bool cta_bucket_sort(unsigned long long* r, int n, unsigned long long* dst, uint32_t* cnt,
+                                uint32_t* red) {
+  const int T = (int)blockDim.x, tid = threadIdx.x;
+  // about two keys per bucket: a power of two in [32, NBMAX]
+  int NB = 32;
+  while (NB < NBMAX && 2 * NB < n) NB <<= 1;
+  uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+  for (int i = tid; i < n; i += T) {
+    const uint32_t h = (uint32_t)(r[i] >> 32);
+    lo = min(lo, h);
+    hi = max(hi, h);
+  }
+  lo = block_min_u32(lo, red);
+  hi = block_max_u32(hi, red);
+  const float scale = (float)NB / ((float)(hi - lo) + 1.0f);
+  auto bucket = [&](unsigned long long key) {
+    return min(NB - 1, (int)((float)((uint32_t)(key >> 32) - lo) * scale));
+  };
+  uint32_t* start = cnt;            // [NB + 1]
+  uint32_t* cur = cnt + NBMAX + 1;  // [NB]
+  for (int b = tid; b < NB; b += T) start[b] = 0u;
+  __syncthreads();
+  for (int i = tid; i < n; i += T) atomicAdd(&start[bucket(r[i])], 1u);
+  __syncthreads();
+  // each thread owns `per` consecutive buckets (threads past NB own none): the largest
+  // bucket and the buckets' sum
+  const int per = NB >= T ? NB / T : 1;
+  const int mine = tid * per < NB ? per : 0;
+  uint32_t mx = 0u, sum = 0u;
+  for (int k = 0; k < mine; ++k) {
+    const uint32_t c = start[tid * per + k];
+    mx = max(mx, c);
+    sum += c;
+  }
+  mx = block_max_u32(mx, red);
+  if (mx > (uint32_t)kMaxBucket) return false;
+  uint32_t total = 0;
+  uint32_t base = block_excl_scan(sum, red, &total);
+  __syncthreads();
+  for (int k = 0; k < mine; ++k) {
+    const int b = tid * per + k;
+    const uint32_t c = start[b];
+    start[b] = base;
+    cur[b] = base;
+    base += c;
+  }
+  if (tid == 0) start[NB] = (uint32_t)n;
+  __syncthreads();
+  for (int i = tid; i < n; i += T) {
+    const unsigned long long key = r[i];
+    dst[atomicAdd(&cur[bucket(key)], 1u)] = key;
+  }
+  __syncthreads();
+  for (int b = tid; b < NB; b += T) {
+    const int s0 = (int)start[b], s1 = (int)start[b + 1];
+    for (int i = s0 + 1; i < s1; ++i) {
+      const unsigned long long x = dst[i];
+      int j = i - 1;
+      while (j >= s0 && dst[j] > x) {
+        dst[j + 1] = dst[j];
+        --j;
+      }
+      dst[j + 1] = x;
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += T) r[i] = dst[i];
+  __syncthreads();
+  return true;
 }
 
 __global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {
@@ -470,6 +590,13 @@ __global__ __launch_bounds__(kSortBigThreads) void k_bin_sort_big(Ws ws) {
     const uint32_t off = ws.bin_off[bin];
     const int n = (int)(ws.bin_off[bin + 1] - off);
     unsigned long long* r = ws.refs + off;
+    __shared__ uint32_t red[32];
+    if (n <= kBucketBigCap &&
+        cta_bucket_sort<kBucketsBig>(r, n, sbuf, reinterpret_cast<uint32_t*>(sbuf + kBucketBigCap), red)) {
+      write_hb_bitmap(ws, r, n, bin);
+      __syncthreads();
+      continue;
+    }
     const int run0 = n <= kSortBigCap ? n : kSortBigCap;
     // sort runs of up to kSortBigCap references in shared memory
     for (int s = 0; s < n; s += run0) {

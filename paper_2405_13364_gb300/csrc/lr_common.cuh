@@ -18,9 +18,20 @@ constexpr int kBin = 1 << kBinLog2;
 constexpr int kHbW = 8, kHbH = 4;           // 8x4 half-blocks (Sec. 2, Stage 3)
 constexpr int kHbPerBin = (kBin / kHbW) * (kBin / kHbH);   // 32
 constexpr float kGuardPx = 16384.0f;        // guard band, pixels
-constexpr int kSortSmemCap = 4096;          // bins below this many refs: k_bin_sort (256 threads)
+constexpr int kSortSmemCap = 2048;          // bins below this many refs: k_bin_sort (256 threads)
 constexpr int kSortBigCap = 8192;           // k_bin_sort_big sorts runs of up to this many refs
 constexpr int kSortBigThreads = 1024;
+// k_bin_sort_big's bucket sort: at most this many buckets per bin, the largest bin sorted
+// this way in shared memory, and the largest bucket sorted by insertion (a bin with a
+// larger bucket, e.g. many equal depths, falls back to the merge sort)
+constexpr int kBucketsBig = 4096;
+constexpr int kBucketBigCap = 20480;
+constexpr int kMaxBucket = 64;
+constexpr size_t kSortSmemBytes = (size_t)kSortSmemCap * 8;
+constexpr size_t kSortBigSmemBytes =
+    (size_t)kBucketBigCap * 8 + (2 * (size_t)kBucketsBig + 2) * 4 > 2 * (size_t)kSortBigCap * 8
+        ? (size_t)kBucketBigCap * 8 + (2 * (size_t)kBucketsBig + 2) * 4
+        : 2 * (size_t)kSortBigCap * 8;
 constexpr int kHistSmemBins = 5120;         // shared-memory bin counters per CTA (Sec. 2 Stage 2)
 constexpr int kChunkQuads = 1024;           // quads per binning CTA
 constexpr int kBinThreads = 256;            // threads per binning CTA

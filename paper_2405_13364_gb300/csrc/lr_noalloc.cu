@@ -130,9 +130,9 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
           prepare_raster_3(&d.blocks_flat, &d.blocks_vtx, &blocks_bwd) != cudaSuccess ||
           overflow_occupancy(&d.ovf_blocks) != cudaSuccess ||
           cudaFuncSetAttribute(k_bin_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(kSortSmemCap * sizeof(unsigned long long))) != cudaSuccess ||
+                               (int)kSortSmemBytes) != cudaSuccess ||
           cudaFuncSetAttribute(k_bin_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(2 * kSortBigCap * sizeof(unsigned long long))) != cudaSuccess)
+                               (int)kSortBigSmemBytes) != cudaSuccess)
         return LR_ERR_CUDA;
       d.scratch = static_cast<unsigned char*>(p);
       d.blocks_flat = d.blocks_flat > 0 ? d.blocks_flat : 1;
@@ -198,8 +198,8 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
   if (chunks > 0) k_bin_count<<<chunks, kBinThreads, 0, st>>>(ws);
   k_bin_scan<<<1, 1024, 0, st>>>(ws);
   if (chunks > 0) k_bin_scatter<<<chunks, kBinThreads, 0, st>>>(ws);
-  k_bin_sort<<<(int)nbins, 256, kSortSmemCap * sizeof(unsigned long long), st>>>(ws);
-  k_bin_sort_big<<<ds.sms, kSortBigThreads, 2 * kSortBigCap * sizeof(unsigned long long), st>>>(ws);
+  k_bin_sort<<<(int)nbins, 256, kSortSmemBytes, st>>>(ws);
+  k_bin_sort_big<<<ds.sms, kSortBigThreads, kSortBigSmemBytes, st>>>(ws);
   const bool vtx_kernel = Q > 0 && vtx;
   if (launch_raster_3(vtx_kernel ? 1 : 0, ws, ds.sms * (vtx_kernel ? ds.blocks_vtx : ds.blocks_flat), st) != cudaSuccess)
     return LR_ERR_CUDA;
