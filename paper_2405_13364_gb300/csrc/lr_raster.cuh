@@ -328,6 +328,20 @@ struct PixelState {
       flagged = true;
       return;
     }
+    if (VTX && K == 1) {       // one slot: branch instead of selecting keys and colours
+      if (x > s[0]) {          // nearer than the held fragment: blend it at once
+        blend(x, xc, V);
+        last = x;
+      } else {
+        if (s[0] != kSent) {
+          blend(s[0], c[0], V);
+          last = s[0];
+        }
+        s[0] = x;
+        c[0] = xc;
+      }
+      return;
+    }
     if (kPrefetch) {
       const float4* cp = reinterpret_cast<const float4*>(V.col) + ((uint32_t)x >> 1);
       if (x > s[0]) {          // nearer than the held fragment: blend it at once
@@ -481,14 +495,14 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
       uint32_t m0 = warp_transpose32(tm0, lane), m1 = warp_transpose32(tm1, lane);
       if (!pix_ok) m0 = m1 = 0;
       // ---- 4. fragments in candidate order through the K-slot sorter -----------------
-      uint32_t bits = m0 | m1;
-      while (bits) {
-        const int c = __ffs(bits) - 1;
-        bits &= bits - 1;
-        // T0 first; T1 as well when both triangles of the quad cover the pixel
-        int t = ((m0 >> c) & 1u) ? 0 : 1;
-        const int last_t = ((m1 >> c) & 1u) ? 1 : 0;
-        for (; t <= last_t; ++t) {
+      // one fragment per iteration: the lowest candidate with a covering triangle, T0
+      // before T1 when both cover the pixel
+      while (m0 | m1) {
+        const int c = __ffs(m0 | m1) - 1;
+        const uint32_t cb = 1u << c;
+        const int t = (m0 & cb) ? 0 : 1;
+        if (t == 0) m0 &= ~cb; else m1 &= ~cb;
+        {
           const TriSm& T = tris[2 * c + t];
           const int4 ea = T.ea, eb = T.eb;
           const float4 kq = T.kq;
