@@ -432,6 +432,7 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
     const uint32_t off = ws.bin_off[bin_g];
     const int n = (int)(ws.bin_off[bin_g + 1] - off);
     const bool vtx_view = V.color_mode == LR_COLOR_VERTEX;
+    const bool hashing = V.hash != nullptr;
 
     PixelState<K, VTX, BWD> st;
     st.init();
@@ -504,16 +505,16 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
         if (t == 0) m0 &= ~cb; else m1 &= ~cb;
         {
           const TriSm& T = tris[2 * c + t];
-          const int4 ea = T.ea, eb = T.eb;
-          const float4 kq = T.kq;
+          const int4 eb = T.eb;
           const uint32_t fl = (uint32_t)eb.z, id = (uint32_t)eb.w;
+          ++cnt;
+          if (hashing) hsh += splitmix64(id);
+          if (st.flagged) continue;
+          const float4 kq = T.kq;
           float l1 = 0.f, l2 = 0.f;
           // (the colour-carrying variant keeps one path: its branch cost more than it saved)
-          const float key = (!VTX && (fl & kTriConstKey)) ? kq.x : tri_key(T, ea, eb, kq, lx, ly, px, py, l1, l2);
+          const float key = (!VTX && (fl & kTriConstKey)) ? kq.x : tri_key(T, T.ea, eb, kq, lx, ly, px, py, l1, l2);
           const unsigned long long sk = ((unsigned long long)__float_as_uint(key) << 32) | id;
-          ++cnt;
-          if (V.hash) hsh += splitmix64(id);
-          if (st.flagged) continue;
           float4 col = make_float4(0.f, 0.f, 0.f, 0.f);
           if (VTX) {
             const float4* qc = qcs + (2 * c + t) * 3;
