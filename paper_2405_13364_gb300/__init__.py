@@ -19,7 +19,7 @@ from . import _binding as B
 from ._binding import (LR_COLOR_FLAT, LR_COLOR_VERTEX, LR_ERR_OVERFLOW, LR_FLAG_TIMING, LR_OK,
                        LrError, lr_camera, lr_config, lr_quads, lr_stats, lr_target, lr_view)
 
-__all__ = ["Renderer", "DeviceScene", "Server", "LrError", "LR_COLOR_FLAT", "LR_COLOR_VERTEX",
+__all__ = ["Renderer", "DeviceScene", "HostStream", "Server", "LrError", "LR_COLOR_FLAT", "LR_COLOR_VERTEX",
            "composite", "load_library"]
 
 
@@ -265,6 +265,82 @@ class GraphBatch:
             self.close()
         except Exception:
             pass
+
+
+class HostStream:
+    """Renders scenes that live in host memory, frame after frame, overlapping each
+    frame's host->device copy of its inputs and the previous frame's device->host read of
+    its image with rendering. Inputs and outputs are host tensors (pinned for overlap);
+    every frame is copied in and its image copied out. One copy stream each way, the
+    renderer on its own stream, `depth` device buffers each way.
+
+        hs = HostStream(renderer, num_vertices, num_quads, indexed, color_mode, num_colors,
+                        width, height)
+        hs.submit(pos, idx, col, view_proj, near, far, out)   # returns at once
+        hs.synchronize()                                       # out holds the image
+    """
+
+    def __init__(self, renderer: "Renderer", num_vertices: int, num_quads: int, indexed: bool,
+                 color_mode: int, num_colors: int, width: int, height: int, depth: int = 2):
+        self.r = renderer
+        self.dev = renderer.device
+        self.width, self.height = int(width), int(height)
+        self.color_mode = int(color_mode)
+        self.depth = int(depth)
+        self.pos = [torch.empty((num_vertices, 3), dtype=torch.float32, device=self.dev) for _ in range(depth)]
+        self.idx = [torch.empty((num_quads, 4), dtype=torch.int32, device=self.dev) if indexed else None
+                    for _ in range(depth)]
+        self.col = [torch.empty((num_colors, 4), dtype=torch.float32, device=self.dev) for _ in range(depth)]
+        self.out = [renderer.make_outputs(width, height) for _ in range(depth)]
+        self.s_in = torch.cuda.Stream(self.dev)
+        self.s_render = torch.cuda.Stream(self.dev)
+        self.s_out = torch.cuda.Stream(self.dev)
+        ev = lambda: [torch.cuda.Event() for _ in range(depth)]
+        self.in_done, self.render_done, self.out_done = ev(), ev(), ev()
+        self.started = [False] * depth
+        self.sized = False
+        self.i = 0
+
+    def submit(self, pos, idx, col, view_proj, near, far, out: torch.Tensor):
+        """Queue one frame: pos f32[V][3], idx i32[Q][4] or None, col f32[Q or V][4] and
+        out f32[H][W][4] are host tensors (pinned for asynchronous copies)."""
+        k = self.i % self.depth
+        self.i += 1
+        if self.started[k]:
+            self.s_in.wait_event(self.render_done[k])     # the slot's inputs are free again
+        with torch.cuda.stream(self.s_in):
+            self.pos[k].copy_(pos, non_blocking=True)
+            if self.idx[k] is not None:
+                self.idx[k].copy_(idx, non_blocking=True)
+            self.col[k].copy_(col, non_blocking=True)
+            self.in_done[k].record(self.s_in)
+        self.s_render.wait_event(self.in_done[k])
+        if self.started[k]:
+            self.s_render.wait_event(self.out_done[k])    # the slot's image was read back
+        vp = view_proj if isinstance(view_proj, tuple) and len(view_proj) == 16 else \
+            tuple(float(x) for x in torch.as_tensor(view_proj, dtype=torch.float32).reshape(-1).tolist())
+        scene = DeviceScene(self.pos[k], self.idx[k], self.col[k], self.color_mode, vp, float(near), float(far))
+        view = Renderer.view_struct(scene, self.width, self.height, self.out[k])
+        # the first frame sizes the workspace (a checked render, which waits for it); later
+        # frames of the same shape reuse it, and synchronize() reports a failed one
+        self.r.render_views([view], stream=self.s_render, check=not self.sized)
+        self.sized = True
+        self.render_done[k].record(self.s_render)
+        self.s_out.wait_event(self.render_done[k])
+        with torch.cuda.stream(self.s_out):
+            out.copy_(self.out[k]["rgba"], non_blocking=True)
+            self.out_done[k].record(self.s_out)
+        self.started[k] = True
+
+    def synchronize(self):
+        """Wait for every queued frame; raises LrError if the last render failed (e.g. a
+        frame that needed more bin references than the first frame sized)."""
+        self.s_in.synchronize()
+        self.s_render.synchronize()
+        self.s_out.synchronize()
+        st = B.lr_get_stats(self.r.ctx, raise_on_error=False)
+        if st.status != LR_OK:
+            raise LrError(st.status, B.lr_last_error(self.r.ctx))
 
 
 class _Composite(torch.autograd.Function):
