@@ -189,7 +189,8 @@ lr_status lr_render_batch(lr_ctx* ctx, int32_t n_views, const lr_view* views, vo
  * lr_graph_create captures the launch sequence of lr_render_batch for these views into a
  * CUDA graph bound to this workspace. lr_graph_launch replays it on a stream; views may
  * be NULL (render the captured views again) or new views with the same shapes (per view:
- * width, height, num_quads, color_mode); scene and output pointers and cameras may change.
+ * width, height, num_quads, color_mode, whether a coverage hash is written); scene and
+ * output pointers and cameras may change.
  * Replays read the view descriptors from one of two pinned host buffers owned by the
  * graph; a launch waits (host side) for the replay two launches back. The graph, its
  * workspace and the context must outlive every replay; lr_get_stats reports the last one. */

@@ -373,15 +373,18 @@ struct Prepared {
   Layout L;
   std::vector<ViewDev> vd;
   bool any_vertex = false;
+  bool any_hash = false;   // a view asks for the coverage hash (selects the hashing rasteriser)
   Ws ws;
   ViewDev* views_dev = nullptr;
 };
 
-static void describe_views(int32_t n_views, const lr_view* views, std::vector<ViewDev>& vd, bool* any_vertex) {
+static void describe_views(int32_t n_views, const lr_view* views, std::vector<ViewDev>& vd, bool* any_vertex,
+                           bool* any_hash) {
   vd.resize(n_views);
   long long qb = 0, pb = 0;
   int bb = 0, cb = 0;
   *any_vertex = false;
+  *any_hash = false;
   for (int i = 0; i < n_views; ++i) {
     const lr_view& v = views[i];
     ViewDev& d = vd[i];
@@ -419,6 +422,7 @@ static void describe_views(int32_t n_views, const lr_view* views, std::vector<Vi
     bb += d.nbx * d.nby;
     cb += (int)((v.quads.num_quads + kChunkQuads - 1) / kChunkQuads);
     *any_vertex |= (v.quads.color_mode == LR_COLOR_VERTEX && v.quads.num_quads > 0);
+    *any_hash |= v.target.cov_hash != nullptr;
   }
 }
 
@@ -434,7 +438,7 @@ static lr_status prepare(lr_ctx* ctx, int32_t n_views, const lr_view* views, voi
   if (s != LR_OK) return s;
   set_capacity(P->L, workspace_bytes);
   if (P->L.refs_cap < 1024) return fail(ctx, LR_ERR_OOM, "workspace too small (see lr_workspace_size)%s");
-  describe_views(n_views, views, P->vd, &P->any_vertex);
+  describe_views(n_views, views, P->vd, &P->any_vertex, &P->any_hash);
   P->ws = make_ws(P->L, workspace, n_views);
   P->views_dev = reinterpret_cast<ViewDev*>(static_cast<char*>(workspace) + P->L.views);
   return LR_OK;
@@ -479,7 +483,7 @@ static lr_status launch_sequence(lr_ctx* ctx, const Prepared& P, cudaStream_t st
   k_bin_sort_big<<<ctx->sms, kSortBigThreads, kSortBigSmemBytes, st>>>(ws);
   rec(ctx, timed, 5, st);
   const bool carry = P.any_vertex || (ctx->cfg.flags & LR_FLAG_CARRY_COLORS);
-  const int mode = bwd ? 2 : (carry ? 1 : 0);
+  const int mode = bwd ? 2 : ((carry ? 1 : 0) | (P.any_hash ? 4 : 0));
   const int rblocks = bwd ? ctx->raster_blocks_bwd : (carry ? ctx->raster_blocks_vtx : ctx->raster_blocks_flat);
   cudaError_t e = ctx->variant->launch(mode, ws, ctx->sms * rblocks, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "raster launch");
@@ -597,14 +601,14 @@ extern "C" lr_status lr_graph_launch(lr_graph* g, const lr_view* views, lr_strea
       const lr_view& a = views[i];
       const lr_view& s0 = g->shape[i];
       if (a.width != s0.width || a.height != s0.height || a.quads.num_quads != s0.quads.num_quads ||
-          a.quads.color_mode != s0.quads.color_mode)
+          a.quads.color_mode != s0.quads.color_mode || (a.target.cov_hash == nullptr) != (s0.target.cov_hash == nullptr))
         return fail(ctx, LR_ERR_INVALID_ARG, "graph launch views must keep the captured shapes%s");
       lr_status s = check_view(ctx, a);
       if (s != LR_OK) return s;
     }
     std::vector<ViewDev> vd;
-    bool any_vertex = false;
-    describe_views(n, views, vd, &any_vertex);
+    bool any_vertex = false, any_hash = false;
+    describe_views(n, views, vd, &any_vertex, &any_hash);
     memcpy(g->staging[b], vd.data(), sizeof(ViewDev) * (size_t)n);
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

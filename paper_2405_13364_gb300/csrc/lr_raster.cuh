@@ -403,7 +403,9 @@ __device__ __forceinline__ void write_pixel(const ViewDev& V, long long pidx, fl
   }
 }
 
-template <int K, bool VTX, bool BWD>
+// HASH: the variant that also writes the per-pixel coverage hash (a test output); the
+// others carry no code or registers for it.
+template <int K, bool VTX, bool BWD, bool HASH>
 __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster(Ws ws) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -432,7 +434,7 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
     const uint32_t off = ws.bin_off[bin_g];
     const int n = (int)(ws.bin_off[bin_g + 1] - off);
     const bool vtx_view = V.color_mode == LR_COLOR_VERTEX;
-    const bool hashing = V.hash != nullptr;
+    const bool hashing = HASH && V.hash != nullptr;
 
     PixelState<K, VTX, BWD> st;
     st.init();
@@ -569,7 +571,7 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
     if (pix_ok) {
       const long long pidx = (long long)py * V.width + px;
       if (!BWD && V.cnt) V.cnt[pidx] = cnt;
-      if (!BWD && V.hash) V.hash[pidx] = hsh;
+      if (!BWD && hashing) V.hash[pidx] = hsh;
       if (!st.flagged) {
         if (!BWD) write_pixel(V, pidx, st.r, st.g, st.b, st.T);
       } else {
@@ -592,35 +594,38 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
 // parallel.
 #define LR_DEFINE_RASTER(KK)                                                                  \
   namespace lr {                                                                              \
+  template <bool VTX, bool BWD, bool HASH>                                                    \
+  static cudaError_t raster_attr_##KK() {                                                     \
+    return cudaFuncSetAttribute(k_raster<KK, VTX, BWD, HASH>,                                 \
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,                  \
+                                (int)raster_smem_bytes(VTX));                                 \
+  }                                                                                           \
   cudaError_t prepare_raster_##KK(int* blocks_flat, int* blocks_vtx, int* blocks_bwd) {       \
-    cudaError_t e = cudaFuncSetAttribute(k_raster<KK, false, false>,                          \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,         \
-                                         (int)raster_smem_bytes(false));                      \
+    cudaError_t e = raster_attr_##KK<false, false, false>();                                  \
+    if (e == cudaSuccess) e = raster_attr_##KK<true, false, false>();                         \
+    if (e == cudaSuccess) e = raster_attr_##KK<false, true, false>();                         \
+    if (e == cudaSuccess) e = raster_attr_##KK<false, false, true>();                         \
+    if (e == cudaSuccess) e = raster_attr_##KK<true, false, true>();                          \
     if (e != cudaSuccess) return e;                                                           \
-    e = cudaFuncSetAttribute(k_raster<KK, true, false>,                                       \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,                     \
-                             (int)raster_smem_bytes(true));                                   \
-    if (e != cudaSuccess) return e;                                                           \
-    e = cudaFuncSetAttribute(k_raster<KK, false, true>,                                       \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,                     \
-                             (int)raster_smem_bytes(false));                                  \
-    if (e != cudaSuccess) return e;                                                           \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_flat, k_raster<KK, false, false>, \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_flat, k_raster<KK, false, false, false>, \
                                                       kRasterThreads, raster_smem_bytes(false)); \
     if (e != cudaSuccess) return e;                                                           \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_bwd, k_raster<KK, false, true>,  \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_bwd, k_raster<KK, false, true, false>, \
                                                       kRasterThreads, raster_smem_bytes(false)); \
     if (e != cudaSuccess) return e;                                                           \
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_vtx, k_raster<KK, true, false>, \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_vtx, k_raster<KK, true, false, false>, \
                                                          kRasterThreads, raster_smem_bytes(true)); \
   }                                                                                           \
+  /* mode: 0 flat colours, 1 colours in the sorter, 2 backward; + 4: coverage hash */        \
   cudaError_t launch_raster_##KK(int mode, const Ws& ws, int grid, cudaStream_t st) {         \
-    if (mode == 1)                                                                            \
-      k_raster<KK, true, false><<<grid, kRasterThreads, raster_smem_bytes(true), st>>>(ws);   \
-    else if (mode == 2)                                                                       \
-      k_raster<KK, false, true><<<grid, kRasterThreads, raster_smem_bytes(false), st>>>(ws);  \
-    else                                                                                      \
-      k_raster<KK, false, false><<<grid, kRasterThreads, raster_smem_bytes(false), st>>>(ws); \
+    const size_t sf = raster_smem_bytes(false), sv = raster_smem_bytes(true);                 \
+    switch (mode) {                                                                           \
+      case 1: k_raster<KK, true, false, false><<<grid, kRasterThreads, sv, st>>>(ws); break;  \
+      case 2: k_raster<KK, false, true, false><<<grid, kRasterThreads, sf, st>>>(ws); break;  \
+      case 4: k_raster<KK, false, false, true><<<grid, kRasterThreads, sf, st>>>(ws); break;  \
+      case 5: k_raster<KK, true, false, true><<<grid, kRasterThreads, sv, st>>>(ws); break;   \
+      default: k_raster<KK, false, false, false><<<grid, kRasterThreads, sf, st>>>(ws); break; \
+    }                                                                                         \
     return cudaGetLastError();                                                                \
   }                                                                                           \
   }
