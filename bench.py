@@ -488,8 +488,8 @@ def run_gpu(args):
     if peaks:
         line["measured_peaks"] = {"hbm_gbs": peaks.get("hbm_gbs")}
         # setup is HBM-bound: algorithmic bytes = 16 B indices + 12 B per vertex (each vertex
-        # read once, shared) + 60 B of records written per quad
-        setup_bytes = 16 * scene.num_quads + 12 * scene.num_vertices + 60 * scene.num_quads
+        # read once, shared) + 80 B of records written per quad
+        setup_bytes = 16 * scene.num_quads + 12 * scene.num_vertices + 80 * scene.num_quads
         if stages.get("setup"):
             gbs = setup_bytes / (stages["setup"] * 1e-3) / 1e9
             line["setup_hbm"] = {"achieved_gbs": round(gbs, 1), "peak_gbs": peaks.get("hbm_gbs"),
