@@ -242,7 +242,7 @@ const char* lr_last_error(const lr_ctx* ctx);
  *    LR_ERR_INVALID_ARG for out-of-range vertex indices); read it after the stream syncs.
  *  - Returns LR_ERR_TOO_LARGE, before any GPU work, when the scene's records plus at least
  *    two bin references per quad do not fit in LR_NOALLOC_SCRATCH_BYTES (roughly: up to
- *    about 500k quads at 1920x1080, or 1M quads at 256x256); LR_ERR_INVALID_ARG for bad
+ *    about 480k quads at 1920x1080, or 550k quads at 256x256); LR_ERR_INVALID_ARG for bad
  *    arguments; LR_ERR_CUDA if a launch or the set-up failed.
  *  - The first call on each device (with that device current) looks up the array's
  *    address and sets kernel attributes; make that first call before any stream capture.
