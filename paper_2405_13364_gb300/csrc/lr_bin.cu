@@ -18,8 +18,8 @@
 //   k_bin_sort     Stage-1 depth sort: sorts each bin's references ascending, i.e. front
 //                  to back by a representative depth, ties with the higher quad index
 //                  first. Bins with fewer than 2048 references: one 256-thread CTA per
-//                  bin, a bitonic network on keys held in registers (exchanges through
-//                  registers, warp shuffles, or shared memory across warps).
+//                  bin, a merge sort in shared memory (warp-sorted 32-key runs, then
+//                  merge-path levels).
 //   k_bin_sort_big The high-density bins (2048 references or more; the paper's "high"
 //                  category): persistent 1024-thread CTAs take them from the front of the
 //                  size-ordered bin list. Up to 20480 references are bucket-sorted in
@@ -313,83 +313,6 @@ __device__ void write_hb_bitmap(const Ws& ws, const unsigned long long* r, int n
   }
 }
 
-// one bitonic step between keys of the same thread (J < E; compile-time register indices)
-template <int E, int J>
-__device__ __forceinline__ void thread_step(unsigned long long (&v)[E], int t, int k) {
-  if (J >= E) return;
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    if (e & J) continue;
-    const int i = E * t + e;
-    const unsigned long long a = v[e], b = v[(e | J) < E ? (e | J) : e];
-    const bool up = (i & k) == 0;
-    const bool sw = up ? (a > b) : (a < b);
-    v[e] = sw ? b : a;
-    v[(e | J) < E ? (e | J) : e] = sw ? a : b;
-  }
-}
-
-// Ascending sort of g[0, n) (n <= E * blockDim.x) by the whole CTA, E keys per thread in
-// registers (element i = E * thread + e; missing elements padded with ~0). Bitonic network:
-// exchanges with a partner in the same thread use registers, in the same warp shuffles,
-// in another warp one round trip through shared memory (sbuf, E * blockDim.x keys).
-template <int E>
-__device__ void cta_sort_regs(unsigned long long* g, int n, unsigned long long* sbuf) {
-  const int t = threadIdx.x;
-  const int N = E * (int)blockDim.x;
-  unsigned long long v[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int i = E * t + e;
-    v[e] = i < n ? g[i] : ~0ull;
-  }
-  for (int k = 2; k <= N; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j >= 32 * E) {                       // partner in another warp
-#pragma unroll
-        for (int e = 0; e < E; ++e) sbuf[E * t + e] = v[e];
-        __syncthreads();
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int i = E * t + e;
-          const unsigned long long w = sbuf[i ^ j];
-          const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
-          v[e] = keep_min ? (v[e] < w ? v[e] : w) : (v[e] > w ? v[e] : w);
-        }
-        __syncthreads();
-      } else if (j >= E) {                     // partner in the same warp
-        const int d = j / E;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int i = E * t + e;
-          const unsigned long long w = __shfl_xor_sync(0xffffffffu, v[e], d);
-          const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
-          v[e] = keep_min ? (v[e] < w ? v[e] : w) : (v[e] > w ? v[e] : w);
-        }
-      } else {                                 // partner in the same thread
-        if (j == 8) thread_step<E, 8>(v, t, k);
-        else if (j == 4) thread_step<E, 4>(v, t, k);
-        else if (j == 2) thread_step<E, 2>(v, t, k);
-        else thread_step<E, 1>(v, t, k);
-      }
-    }
-  }
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int i = E * t + e;
-    if (i < n) g[i] = v[e];
-  }
-}
-
-// dispatch on the number of keys per thread (powers of two up to 16)
-__device__ void cta_sort(unsigned long long* g, int n, unsigned long long* sbuf) {
-  const int per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
-  if (per <= 1) cta_sort_regs<1>(g, n, sbuf);
-  else if (per <= 2) cta_sort_regs<2>(g, n, sbuf);
-  else if (per <= 4) cta_sort_regs<4>(g, n, sbuf);
-  else cta_sort_regs<8>(g, n, sbuf);
-}
-
 // Block-wide reduction / exclusive scan helpers over all threads of the CTA (blockDim a
 // multiple of 32, at most 1024); red holds 32 words of shared scratch.
 __device__ __forceinline__ uint32_t block_min_u32(uint32_t v, uint32_t* red) {
@@ -509,21 +432,6 @@ __device__ bool cta_bucket_sort(unsigned long long* r, int n, unsigned long long
   return true;
 }
 
-__global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {
-  extern __shared__ unsigned long long sbuf[];
-  if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
-  const int bin = blockIdx.x;
-  const uint32_t off = ws.bin_off[bin];
-  const int n = (int)(ws.bin_off[bin + 1] - off);
-  if (n >= kSortSmemCap) return;   // high-density: k_bin_sort_big
-  unsigned long long* r = ws.refs + off;
-  if (n > 1) {
-    cta_sort(r, n, sbuf);
-    __syncthreads();
-  }
-  write_hb_bitmap(ws, r, n, bin);
-}
-
 // Ascending merge sort of g[0, n) (n <= kSortBigCap) in shared memory by the whole CTA:
 // 32-key runs sorted by warp shuffles, then merge levels between two shared buffers, each
 // thread producing an equal slice of every level's output (merge path search + a
@@ -571,6 +479,21 @@ __device__ void cta_merge_sort_smem(unsigned long long* g, int n, unsigned long 
     unsigned long long* tmp = src; src = dst; dst = tmp;
   }
   for (int i = t; i < n; i += T) g[i] = src[i];
+}
+
+__global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {
+  extern __shared__ unsigned long long sbuf[];
+  if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
+  const int bin = blockIdx.x;
+  const uint32_t off = ws.bin_off[bin];
+  const int n = (int)(ws.bin_off[bin + 1] - off);
+  if (n >= kSortSmemCap) return;   // high-density: k_bin_sort_big
+  unsigned long long* r = ws.refs + off;
+  if (n > 1) {
+    cta_merge_sort_smem(r, n, sbuf, sbuf + kSortSmemCap);
+    __syncthreads();
+  }
+  write_hb_bitmap(ws, r, n, bin);
 }
 
 __global__ __launch_bounds__(kSortBigThreads) void k_bin_sort_big(Ws ws) {

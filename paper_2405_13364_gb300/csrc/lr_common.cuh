@@ -27,7 +27,7 @@ constexpr int kSortBigThreads = 1024;
 constexpr int kBucketsBig = 4096;
 constexpr int kBucketBigCap = 20480;
 constexpr int kMaxBucket = 64;
-constexpr size_t kSortSmemBytes = (size_t)kSortSmemCap * 8;
+constexpr size_t kSortSmemBytes = 2 * (size_t)kSortSmemCap * 8;
 constexpr size_t kSortBigSmemBytes =
     (size_t)kBucketBigCap * 8 + (2 * (size_t)kBucketsBig + 2) * 4 > 2 * (size_t)kSortBigCap * 8
         ? (size_t)kBucketBigCap * 8 + (2 * (size_t)kBucketsBig + 2) * 4
