@@ -74,7 +74,7 @@ static const RasterVariant kVariants[] = {
 };
 
 struct Layout {
-  size_t ctrl, views, rec, rec_rect, rec_info, rec_rep, bin_count, bin_off, bin_cursor, bin_order;
+  size_t ctrl, views, rec, rec_rect, rec_info, rec_rep, bin_count, bin_off, bin_cursor, bin_order, chunk_span;
   size_t refs, refs_tmp, ref_hb, ovf_list, total;
   long long total_quads = 0, total_pix = 0, refs_cap = 0;
   int total_bins = 0, total_chunks = 0;
@@ -105,6 +105,7 @@ static Layout make_layout(int n, const long long* Q, const int* W, const int* H)
   L.bin_count = take(sizeof(uint32_t) * (size_t)L.total_bins);
   L.bin_off = take(sizeof(uint32_t) * ((size_t)L.total_bins + 1));
   L.bin_cursor = take(sizeof(uint32_t) * (size_t)L.total_bins);
+  L.chunk_span = take(sizeof(uint2) * (size_t)L.total_chunks);
   L.bin_order = take(sizeof(uint32_t) * (size_t)L.total_bins);
   L.ovf_list = take(sizeof(uint32_t) * (size_t)L.total_pix);
   L.refs = o;      // refs and refs_tmp follow; see set_capacity
@@ -157,6 +158,7 @@ static Ws make_ws(const Layout& L, void* base, int n_views) {
   w.bin_count = reinterpret_cast<uint32_t*>(b + L.bin_count);
   w.bin_off = reinterpret_cast<uint32_t*>(b + L.bin_off);
   w.bin_cursor = reinterpret_cast<uint32_t*>(b + L.bin_cursor);
+  w.chunk_span = reinterpret_cast<uint2*>(b + L.chunk_span);
   w.bin_order = reinterpret_cast<uint32_t*>(b + L.bin_order);
   w.refs = reinterpret_cast<unsigned long long*>(b + L.refs);
   w.refs_tmp = reinterpret_cast<unsigned long long*>(b + L.refs_tmp);

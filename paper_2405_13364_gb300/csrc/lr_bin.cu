@@ -11,9 +11,10 @@
 //   k_bin_scan     Phase 2: exclusive scan of the counts into list offsets, capacity
 //                  check, and a categorisation of bins by size (the paper's empty / low /
 //                  high) that orders the rasteriser's work queue, largest bins first.
-//   k_bin_scatter  Phase 3: recomputes the chunk's counters, reserves one range per
-//                  (chunk, bin) with a global atomic, then places references with shared
-//                  memory atomics. A reference is a 64-bit sort key:
+//   k_bin_scatter  Phase 3: places the chunk's references, each (chunk, bin) in the range
+//                  k_bin_count reserved for it (k_bin_count's global atomic returns the
+//                  range's base, listed per chunk), slots by shared-memory atomics. A
+//                  reference is a 64-bit sort key:
 //                  (~representative 1/w) << 32 | ~record index.
 //   k_bin_sort     Stage-1 depth sort: sorts each bin's references ascending, i.e. front
 //                  to back by a representative depth, ties with the higher quad index
@@ -140,9 +141,31 @@ __global__ __launch_bounds__(kBinThreads) void k_bin_count(Ws ws) {
     else atomicAdd(&ws.bin_count[V.bin_base + b], 1u);
   });
   __syncthreads();
-  if (smem)
-    for (int b = threadIdx.x; b < nb; b += blockDim.x)
-      if (hist[b]) atomicAdd(&ws.bin_count[V.bin_base + b], hist[b]);
+  if (!smem) return;
+  // reserve the chunk's range in every bin it touches, and list (bin, base of the range)
+  // for k_bin_scatter, which then places references without recounting
+  __shared__ uint32_t s_n, s_start, s_pos;
+  if (threadIdx.x == 0) { s_n = 0; s_pos = 0; }
+  __syncthreads();
+  uint32_t mine = 0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) mine += hist[b] != 0u;
+  if (mine) atomicAdd(&s_n, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_start = (uint32_t)min(atomicAdd(&ws.ctrl->chunk_list_head, (unsigned long long)s_n), 0xFFFFFFFFull);
+    ws.chunk_span[blockIdx.x] = make_uint2(s_start, s_n);
+  }
+  __syncthreads();
+  uint2* list = reinterpret_cast<uint2*>(ws.refs_tmp);
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const uint32_t c = hist[b];
+    if (!c) continue;
+    const uint32_t base = atomicAdd(&ws.bin_count[V.bin_base + b], c);
+    const unsigned long long at = (unsigned long long)s_start + atomicAdd(&s_pos, 1u);
+    // a list past the reference capacity means the references do not fit either: the scan
+    // reports the overflow and the scatter does not run
+    if (at < (unsigned long long)ws.refs_cap) list[at] = make_uint2((uint32_t)b, base);
+  }
 }
 
 // Single CTA. Offsets (exclusive scan), capacity check, and the bin order for the
@@ -237,13 +260,13 @@ __global__ __launch_bounds__(kBinThreads) void k_bin_scatter(Ws ws) {
   const int nb = V.nbx * V.nby;
   const bool smem = nb <= kHistSmemBins;
   if (smem) {
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0u;
-    __syncthreads();
-    for_each_ref(ws, V, q0, q1, [&](long long, int b, int, int, uint2, uint32_t) { atomicAdd(&hist[b], 1u); });
-    __syncthreads();
-    // reserve one contiguous range per touched bin
-    for (int b = threadIdx.x; b < nb; b += blockDim.x)
-      if (hist[b]) hist[b] = atomicAdd(&ws.bin_cursor[V.bin_base + b], hist[b]);
+    // the chunk's range in each bin it touches, reserved by k_bin_count
+    const uint2 sp = ws.chunk_span[blockIdx.x];
+    const uint2* list = reinterpret_cast<const uint2*>(ws.refs_tmp) + sp.x;
+    for (int i = threadIdx.x; i < (int)sp.y; i += blockDim.x) {
+      const uint2 e = list[i];
+      hist[e.x] = ws.bin_off[V.bin_base + e.x] + e.y;
+    }
     __syncthreads();
   }
   for_each_ref(ws, V, q0, q1, [&](long long q, int b, int bx, int by, uint2 rect, uint32_t info) {

@@ -92,7 +92,8 @@ struct Ctrl {
   unsigned long long bins_nonempty;
   unsigned long long bins_high;
   unsigned long long max_bin;
-  unsigned long long pad[8];
+  unsigned long long chunk_list_head;   // allocation cursor of the chunks' (bin, base) lists
+  unsigned long long pad[7];
 };
 
 // The per-quad record written by k_setup and gathered by every later stage, 64 bytes so
@@ -136,6 +137,8 @@ struct Ws {
   uint32_t* bin_count;       // [total_bins]
   uint32_t* bin_off;         // [total_bins + 1]
   uint32_t* bin_cursor;      // [total_bins]
+  uint2* chunk_span;         // [total_chunks] (start, length) of the chunk's list of (bin, base
+                             // of the chunk's range within the bin), kept in refs_tmp
   uint32_t* bin_order;       // [total_bins]: bins by decreasing reference count
   unsigned long long* refs;      // [refs_cap] sorted per bin: (~rep_bits << 32) | ~record
   unsigned long long* refs_tmp;  // [refs_cap] merge buffer of the high-density sort

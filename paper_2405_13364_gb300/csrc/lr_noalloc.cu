@@ -101,6 +101,7 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
   const size_t o_cnt = o; o = up256(o + 4 * (size_t)nbins);
   const size_t o_off = o; o = up256(o + 4 * ((size_t)nbins + 1));
   const size_t o_cur = o; o = up256(o + 4 * (size_t)nbins);
+  const size_t o_span = o; o = up256(o + 8 * (size_t)((Q + kChunkQuads - 1) / kChunkQuads));
   const size_t o_ord = o; o = up256(o + 4 * (size_t)nbins);
   const size_t o_ovf = o; o = up256(o + 4 * (size_t)npix);
   if (o >= (size_t)LR_NOALLOC_SCRATCH_BYTES) return LR_ERR_TOO_LARGE;
@@ -183,6 +184,7 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
   ws.bin_count = reinterpret_cast<uint32_t*>(base + o_cnt);
   ws.bin_off = reinterpret_cast<uint32_t*>(base + o_off);
   ws.bin_cursor = reinterpret_cast<uint32_t*>(base + o_cur);
+  ws.chunk_span = reinterpret_cast<uint2*>(base + o_span);
   ws.bin_order = reinterpret_cast<uint32_t*>(base + o_ord);
   ws.refs = reinterpret_cast<unsigned long long*>(base + o_refs);
   ws.refs_tmp = reinterpret_cast<unsigned long long*>(base + o_tmp);
