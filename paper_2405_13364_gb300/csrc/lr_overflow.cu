@@ -4,9 +4,9 @@
 // conservative algorithm" (Sec. 2, "Sample blending"; Sec. 3, "Fragment sorting errors").
 //
 // One warp per registered pixel. The warp takes the candidates of the pixel's half-block
-// from the bin's transposed bitmap (one coalesced load per 1024 references), keeps those
-// whose box holds the pixel, re-evaluates their fragments exactly (64-bit edge tests, the
-// same depth key as the rasteriser), sorts them fully and composites front to back. The
+// from the bin's transposed bitmap (one coalesced load per 1024 references),
+// re-evaluates their fragments exactly (64-bit edge tests, the same depth key as the
+// rasteriser), sorts them fully and composites front to back. The
 // overflow pixels of a frame are few and all run in one wave, so the kernel's time is one
 // warp's chain of dependent loads: the bitmap keeps that chain to a few loads per 32
 // candidates. Memory is bounded: a pass keeps the kOvfKeep nearest fragments below a
@@ -189,14 +189,9 @@ __device__ void overflow_pixel(const Ws& ws, long long pid, unsigned long long* 
       br.prepare(g + lane < nw ? __ldg(row + g + lane) : 0u, lane);
       for (int r0 = 0; r0 < br.total; r0 += 32) {
         const int j = br.get(r0, lane);
-        bool hit = false;
-        uint32_t rec = 0;
-        if (j >= 0) {
-          rec = ~(uint32_t)ws.refs[off + 32 * g + j];
-          const uint2 r = ws.rec_rect[rec];
-          hit = (int)(r.x & 0xffff) <= px && (int)(r.x >> 16) >= px && (int)(r.y & 0xffff) <= py &&
-                (int)(r.y >> 16) >= py;
-        }
+        // candidates of the pixel's half-block; the exact test below decides coverage
+        const bool hit = j >= 0;
+        const uint32_t rec = hit ? ~(uint32_t)ws.refs[off + 32 * g + j] : 0u;
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
           unsigned long long sk = 0;
