@@ -42,8 +42,8 @@ LAUNCHES_PER_FRAME = 10
 # (workload, K, carried colours), with the hash of the rasteriser sources they were taken
 # on: the figure is reported only while the kernel is unchanged.
 RASTER_TRAFFIC = {
-    ("layers", 1, False): (111_932_672, "2b2af4cc8698620b"),     # profiles/k_raster_layers1080p.md
-    ("particles", 1, False): (414_546_176, "2b2af4cc8698620b"),  # profiles/k_raster_particles1080p.md
+    ("layers", 1, False): (111_365_120, "cd81f8ff0c09f16a"),     # profiles/k_raster_layers1080p.md
+    ("particles", 1, False): (413_398_016, "cd81f8ff0c09f16a"),  # profiles/k_raster_particles1080p.md
 }
 RASTER_SOURCES = ("lr_raster.cuh", "lr_common.cuh")
 LANES_PER_SM_CLK = 128
