@@ -310,7 +310,11 @@ __device__ void cta_merge(const unsigned long long* a, int na, const unsigned lo
 // computed one warp per 32 references and transposed across the warp, so that row h, word
 // w holds the bits of references 32 w .. 32 w + 31 for half-block h. The rasteriser then
 // reads a half-block's candidates with one coalesced load per 1024 references.
-__device__ void write_hb_bitmap(const Ws& ws, const unsigned long long* r, int n, int bin) {
+// When the bitmap fits `stage` (shared memory, stage_words 32-bit words), the transposed
+// words are assembled there and copied out row by row with coalesced stores; otherwise each
+// lane stores its word of a row directly.
+__device__ void write_hb_bitmap(const Ws& ws, const unsigned long long* r, int n, int bin, uint32_t* stage,
+                                int stage_words) {
   const int v = view_of_bin(ws.views, ws.n_views, bin);
   const ViewDev& V = ws.views[v];
   const int b = bin - V.bin_base;
@@ -318,6 +322,8 @@ __device__ void write_hb_bitmap(const Ws& ws, const unsigned long long* r, int n
   const int nw = (n + 31) >> 5;
   const int lane = threadIdx.x & 31;
   uint32_t* bm = ws.ref_hb + (r - ws.refs) + 32 * (size_t)bin;
+  const bool staged = 32 * nw <= stage_words;
+  uint32_t* dst = staged ? stage : bm;
   for (int w = threadIdx.x >> 5; w < nw; w += blockDim.x >> 5) {
     const int i = 32 * w + lane;
     uint32_t mask = 0;
@@ -332,7 +338,11 @@ __device__ void write_hb_bitmap(const Ws& ws, const unsigned long long* r, int n
         for (int hy = hy0; hy <= hy1; ++hy) mask |= row << (hy * (kBin / kHbW));
       }
     }
-    bm[(size_t)lane * nw + w] = warp_transpose32(mask, lane);
+    dst[(size_t)lane * nw + w] = warp_transpose32(mask, lane);
+  }
+  if (staged) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < 32 * nw; i += blockDim.x) bm[i] = stage[i];
   }
 }
 
@@ -516,7 +526,7 @@ __global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {
     cta_merge_sort_smem(r, n, sbuf, sbuf + kSortSmemCap);
     __syncthreads();
   }
-  write_hb_bitmap(ws, r, n, bin);
+  write_hb_bitmap(ws, r, n, bin, reinterpret_cast<uint32_t*>(sbuf), (int)(kSortSmemBytes / 4));
 }
 
 __global__ __launch_bounds__(kSortBigThreads) void k_bin_sort_big(Ws ws) {
@@ -539,7 +549,7 @@ __global__ __launch_bounds__(kSortBigThreads) void k_bin_sort_big(Ws ws) {
     __shared__ uint32_t red[32];
     if (n <= kBucketBigCap &&
         cta_bucket_sort<kBucketsBig>(r, n, sbuf, reinterpret_cast<uint32_t*>(sbuf + kBucketBigCap), red)) {
-      write_hb_bitmap(ws, r, n, bin);
+      write_hb_bitmap(ws, r, n, bin, reinterpret_cast<uint32_t*>(sbuf), (int)(kSortBigSmemBytes / 4));
       __syncthreads();
       continue;
     }
@@ -565,7 +575,7 @@ __global__ __launch_bounds__(kSortBigThreads) void k_bin_sort_big(Ws ws) {
       for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = src[i];
     }
     __syncthreads();
-    write_hb_bitmap(ws, r, n, bin);
+    write_hb_bitmap(ws, r, n, bin, reinterpret_cast<uint32_t*>(sbuf), (int)(kSortBigSmemBytes / 4));
     __syncthreads();
   }
 }
