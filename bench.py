@@ -42,8 +42,9 @@ LAUNCHES_PER_FRAME = 10
 # (workload, K, carried colours), with the hash of the rasteriser sources they were taken
 # on: the figure is reported only while the kernel is unchanged.
 RASTER_TRAFFIC = {
-    ("layers", 1, False): (111_365_120, "cd81f8ff0c09f16a"),     # profiles/k_raster_layers1080p.md
-    ("particles", 1, False): (413_398_016, "cd81f8ff0c09f16a"),  # profiles/k_raster_particles1080p.md
+    # (DRAM read + write bytes per launch, ncu smsp__issue_active, source hash)
+    ("layers", 1, False): (111_365_120, 0.726, "cd81f8ff0c09f16a"),     # profiles/k_raster_layers1080p.md
+    ("particles", 1, False): (413_398_016, 0.686, "cd81f8ff0c09f16a"),  # profiles/k_raster_particles1080p.md
 }
 RASTER_SOURCES = ("lr_raster.cuh", "lr_common.cuh")
 LANES_PER_SM_CLK = 128
@@ -96,11 +97,13 @@ def raster_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def raster_traffic(workload: str, k: int, carry: bool):
+def raster_capture(workload: str, k: int, carry: bool):
+    """(traffic bytes, issue-slot utilisation) of the committed ncu capture of this
+    rasteriser build, or (None, None) once the sources differ from the captured build."""
     t = RASTER_TRAFFIC.get((workload, k, carry))
-    if t is None or t[1] != raster_source_hash():
-        return None
-    return t[0]
+    if t is None or t[2] != raster_source_hash():
+        return None, None
+    return t[0], t[1]
 
 
 class ClockSampler:
@@ -472,7 +475,8 @@ def run_gpu(args):
         "overflow_pixels": st0["overflow_pixels"],
         "roofline": {"bound": "alu", "kernel": "k_raster", "achieved": round(achieved, 4),
                      "peak": round(peak, 3), "unit": "Tlane-op/s", "frac": round(achieved / peak, 4),
-                     "traffic": raster_traffic(args.workload, args.k, carry),
+                     "traffic": raster_capture(args.workload, args.k, carry)[0],
+                     "ncu_issue_active": raster_capture(args.workload, args.k, carry)[1],
                      "ops_per_fragment": OPS_PER_FRAG_BASE + args.k,
                      "peak_basis": f"{SM_COUNT} SMs x 128 lanes x {sm_max:.0f} MHz (max SM clock)"},
         "setup_hbm": None,
