@@ -460,13 +460,19 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
 #pragma unroll 1
         for (int t = 0; t < 2; ++t) {
           TriSm& T = tris[2 * lane + t];
-          int cor[3], box[4], le[3], lsx[3], lsy[3];
-          const bool ok = (R.info & (kInfoSmall0 << t))
-                              ? setup_tri_small(T, R.X, R.Y, R.q, R.inv[t], R.info, t, jl, ox, oy, cor, box, le, lsx, lsy)
-                              : setup_tri(T, R.X, R.Y, R.q, R.info, t, jl, ox, oy, cor, box, le, lsx, lsy);
-          if (!ok) continue;
-          const uint32_t mk = ((uint32_t)T.eb.z & kTriFast) ? tri_mask_fast(le, lsx, lsy, box)
-                                                            : tri_mask_slow(T, ox, oy, box);
+          int cor[3];
+          uint32_t mk;
+          if (R.info & (kInfoSmall0 << t)) {
+            // arrays of their own, never passed out of line: they stay in registers
+            int box[4], le[3], lsx[3], lsy[3];
+            if (!setup_tri_small(T, R.X, R.Y, R.q, R.inv[t], R.info, t, jl, ox, oy, cor, box, le, lsx, lsy)) continue;
+            mk = tri_mask_fast(le, lsx, lsy, box);
+          } else {
+            int cg[3], box[4], le[3], lsx[3], lsy[3];
+            if (!setup_tri(T, R.X, R.Y, R.q, R.info, t, jl, ox, oy, cg, box, le, lsx, lsy)) continue;
+            mk = ((uint32_t)T.eb.z & kTriFast) ? tri_mask_fast(le, lsx, lsy, box) : tri_mask_slow(T, ox, oy, box);
+            cor[0] = cg[0]; cor[1] = cg[1]; cor[2] = cg[2];
+          }
           if (t == 0) tm0 = mk; else tm1 = mk;
           if (VTX) {
             float4* qc = qcs + (2 * lane + t) * 3;
