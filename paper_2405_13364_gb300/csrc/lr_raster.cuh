@@ -468,8 +468,9 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
             if (!setup_tri_small(T, R.X, R.Y, R.q, R.inv[t], R.info, t, jl, ox, oy, cor, box, le, lsx, lsy)) continue;
             mk = tri_mask_fast(le, lsx, lsy, box);
           } else {
+            const QuadRec G = R;   // the out-of-line path's own copy (its address escapes)
             int cg[3], box[4], le[3], lsx[3], lsy[3];
-            if (!setup_tri(T, R.X, R.Y, R.q, R.info, t, jl, ox, oy, cg, box, le, lsx, lsy)) continue;
+            if (!setup_tri(T, G.X, G.Y, G.q, G.info, t, jl, ox, oy, cg, box, le, lsx, lsy)) continue;
             mk = ((uint32_t)T.eb.z & kTriFast) ? tri_mask_fast(le, lsx, lsy, box) : tri_mask_slow(T, ox, oy, box);
             cor[0] = cg[0]; cor[1] = cg[1]; cor[2] = cg[2];
           }
