@@ -465,7 +465,9 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
           if (R.info & (kInfoSmall0 << t)) {
             // arrays of their own, never passed out of line: they stay in registers
             int box[4], le[3], lsx[3], lsy[3];
-            if (!setup_tri_small(T, R.X, R.Y, R.q, R.inv[t], R.info, t, jl, ox, oy, cor, box, le, lsx, lsy)) continue;
+            if (!setup_tri_small(T, R.X, R.Y, R.q, t ? R.inv[1] : R.inv[0], R.info, t, jl, ox, oy, cor, box, le, lsx,
+                                 lsy))
+              continue;
             mk = tri_mask_fast(le, lsx, lsy, box);
           } else {
             const QuadRec G = R;   // the out-of-line path's own copy (its address escapes)
