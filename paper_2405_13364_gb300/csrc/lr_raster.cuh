@@ -455,8 +455,6 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
       if (lane < nc) {
         const QuadRec R = load_rec(ws.rec, rec);
         const uint32_t jl = (uint32_t)(rec - V.quad_base);
-        uint4 vi = make_uint4(4 * jl, 4 * jl + 1, 4 * jl + 2, 4 * jl + 3);
-        if (VTX && vtx_view && V.idx) vi = __ldg(reinterpret_cast<const uint4*>(V.idx) + jl);
 #pragma unroll 1
         for (int t = 0; t < 2; ++t) {
           TriSm& T = tris[2 * lane + t];
@@ -485,6 +483,8 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
             } else {
               // corner colours times 1/w as (c0, c1 - c0, c2 - c0) for the fragment's
               // c0 + l1 (c1 - c0) + l2 (c2 - c0)
+              uint4 vi = make_uint4(4 * jl, 4 * jl + 1, 4 * jl + 2, 4 * jl + 3);
+              if (V.idx) vi = __ldg(reinterpret_cast<const uint4*>(V.idx) + jl);
               float4 a[3];
 #pragma unroll
               for (int k = 0; k < 3; ++k) {
