@@ -43,8 +43,8 @@ LAUNCHES_PER_FRAME = 10
 # on: the figure is reported only while the kernel is unchanged.
 RASTER_TRAFFIC = {
     # (DRAM read + write bytes per launch, ncu smsp__issue_active, source hash)
-    ("layers", 1, False): (111_365_120, 0.726, "cd81f8ff0c09f16a"),     # profiles/k_raster_layers1080p.md
-    ("particles", 1, False): (413_398_016, 0.686, "cd81f8ff0c09f16a"),  # profiles/k_raster_particles1080p.md
+    ("layers", 1, False): (102_366_208, 0.768, "9db22f6ee77ee52b"),     # profiles/k_raster_layers1080p.md
+    ("particles", 1, False): (390_256_640, 0.724, "9db22f6ee77ee52b"),  # profiles/k_raster_particles1080p.md
 }
 RASTER_SOURCES = ("lr_raster.cuh", "lr_common.cuh")
 LANES_PER_SM_CLK = 128
