@@ -268,6 +268,47 @@ def serving_benchmark(P, torch, num_requests=256, rate_hz=200.0, seed=0):
     }
 
 
+def differentiable_benchmark(P, torch, steps: int, sorter_k: int = 1):
+    """Differentiable compositing on the 1024x1024 layer scene (524,288 quads, flat RGBA):
+    each step renders the image, forms dL/dC = 2 (C - T) for the squared L2 distance to a
+    target rendered with perturbed colours, and runs the backward (per-quad RGBA
+    gradients, bins and per-pixel order recomputed), all on the device. Reports forward,
+    backward and step times (CUDA events)."""
+    import scenegen
+    s = scenegen.config_diff_1024()
+    ds = P.DeviceScene.from_scene(s)
+    r = P.Renderer(sorter_k=sorter_k)
+    tgt = r.render(ds.with_colors(torch.tensor(scenegen.perturbed_target_colors(s.colors, seed=1),
+                                               device=ds.colors.device)), s.width, s.height)["rgba"]
+    out = r.make_outputs(s.width, s.height)
+    view = r.view_struct(ds, s.width, s.height, out)
+    st = r.render_views([view])                        # sizes the workspace
+    frags = int(st.fragments)
+    g = torch.zeros_like(out["rgba"])
+    r.render_backward(ds, s.width, s.height, out["rgba"], g)   # sizes it for the backward too
+    stream = torch.cuda.current_stream()
+    fwd, bwd = [], []
+    for i in range(steps + 3):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        r.render_views([view], check=False)
+        g[..., :3] = 2.0 * (out["rgba"][..., :3] - tgt[..., :3])
+        e1.record(stream)
+        r.render_backward(ds, s.width, s.height, out["rgba"], g, check=False)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        if i >= 3:
+            fwd.append(e0.elapsed_time(e1))
+            bwd.append(e1.elapsed_time(e2))
+    r.close()
+    f, b = statistics.median(fwd), statistics.median(bwd)
+    return {"workload": "1024x1024, 524,288 quads (layer generator, flat RGBA), loss = squared L2 to a "
+                        "target with RGBA + N(0, 0.05)",
+            "fragments": frags, "forward_ms": round(f, 4), "backward_ms": round(b, 4),
+            "step_ms": round(f + b, 4), "backward_gfrag_s": round(frags / (b * 1e-3) / 1e9, 2),
+            "steps": steps, "sorter_k": sorter_k}
+
+
 def run_reference(args):
     """The CPU oracle on this host's cores, same workload and metric."""
     rank, world, _ = _env_rank()
@@ -432,8 +473,10 @@ def run_gpu(args):
         return
 
     serving = None
+    differentiable = None
     if args.workload == "layers" and world == 1 and not args.no_serving:
         serving = serving_benchmark(P, torch)
+        differentiable = differentiable_benchmark(P, torch, steps=20)
 
     stages = {k: round(v / args.steps, 4) for k, v in stage_sum.items()}
     raster_ms = stages["raster"]
@@ -486,6 +529,7 @@ def run_gpu(args):
                 "api": "HostStream (copies of neighbouring frames overlap rendering)",
                 "serial_ms_per_step": round(e2e_serial_ms, 4)},
         "served_stream": serving,
+        "differentiable": differentiable,
         "gpu_launches": LAUNCHES_PER_FRAME * args.steps,
         "clocks": clocks,
     }
