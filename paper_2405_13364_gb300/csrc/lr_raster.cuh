@@ -62,10 +62,12 @@ struct __align__(16) TriSm {
   int pad[2];
 };
 
-// dynamic shared memory of k_raster: per warp 64 triangle records and, when fragments
-// carry colours, 3 premultiplied vertex colours per triangle
-__host__ __device__ constexpr size_t raster_smem_bytes(bool vtx) {
-  return (size_t)kRasterWarps * 64 * sizeof(TriSm) + (vtx ? (size_t)kRasterWarps * 64 * 3 * sizeof(float4) : 0);
+// dynamic shared memory of k_raster: per warp 64 triangle records, when fragments carry
+// colours 3 premultiplied vertex colours per triangle, and for the backward 32 gradient
+// slots
+__host__ __device__ constexpr size_t raster_smem_bytes(bool vtx, bool bwd = false) {
+  return (size_t)kRasterWarps * 64 * sizeof(TriSm) + (vtx ? (size_t)kRasterWarps * 64 * 3 * sizeof(float4) : 0) +
+         (bwd ? (size_t)kRasterWarps * 32 * sizeof(float4) : 0);
 }
 
 // exact 64-bit edge values (unbiased) of a triangle at pixel (px, py)
@@ -192,6 +194,7 @@ struct GradPixel {
   float gr, gg, gb, ga;      // dL/d(R, G, B, A) of the pixel
   float fr, fg, fb, fT;      // forward colour and transmittance
   float* grad;               // f32[Q][4] of the view
+  float4* agg;               // this warp's 32 shared-memory slots for combining lanes' gradients
 };
 
 // Columns lx in [0, 8) of one half-block row where an edge is non-negative, as an 8-bit
@@ -314,11 +317,26 @@ struct PixelState {
         da -= (gp.gr * (gp.fr - r) + gp.gg * (gp.fg - g) + gp.gb * (gp.fb - b)) * inv;
         da += gp.ga * gp.fT * inv;
       }
-      float* gq = gp.grad + 4ull * j;
-      atomicAdd(gq + 0, gp.gr * w);
-      atomicAdd(gq + 1, gp.gg * w);
-      atomicAdd(gq + 2, gp.gb * w);
-      atomicAdd(gq + 3, da);
+      // lanes blending a fragment of the same quad at this point add their contributions
+      // in shared memory first, and one of them issues the four global atomics
+      const int lane = threadIdx.x & 31;
+      const unsigned act = __activemask();
+      const unsigned grp = __match_any_sync(act, j);
+      gp.agg[lane] = make_float4(gp.gr * w, gp.gg * w, gp.gb * w, da);
+      __syncwarp(act);
+      if (lane == __ffs(grp) - 1) {
+        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (unsigned m = grp; m; m &= m - 1) {
+          const float4 c = gp.agg[__ffs(m) - 1];
+          sum.x += c.x; sum.y += c.y; sum.z += c.z; sum.w += c.w;
+        }
+        float* gq = gp.grad + 4ull * j;
+        atomicAdd(gq + 0, sum.x);
+        atomicAdd(gq + 1, sum.y);
+        atomicAdd(gq + 2, sum.z);
+        atomicAdd(gq + 3, sum.w);
+      }
+      __syncwarp(act);
     }
     T *= 1.0f - col.w;
   }
@@ -412,6 +430,7 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
   const int lx = lane & (kHbW - 1), ly = lane >> 3;
   TriSm* tris = reinterpret_cast<TriSm*>(smem) + warp * 64;
   float4* qcs = reinterpret_cast<float4*>(smem + (size_t)kRasterWarps * 64 * sizeof(TriSm)) + (size_t)warp * 64 * 3;
+  float4* agg = reinterpret_cast<float4*>(smem + raster_smem_bytes(VTX, false)) + (size_t)warp * 32;
   if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
   const unsigned long long nitems = ws.ctrl->raster_items;
   unsigned long long frag_total = 0;
@@ -439,6 +458,7 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
     PixelState<K, VTX, BWD> st;
     st.init();
     st.gp.grad = nullptr;
+    st.gp.agg = agg;
     if (BWD && pix_ok) {
       const long long pidx = (long long)py * V.width + px;
       const float4 gq = reinterpret_cast<const float4*>(ws.grad_out)[pidx];
@@ -607,7 +627,7 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
   static cudaError_t raster_attr_##KK() {                                                     \
     return cudaFuncSetAttribute(k_raster<KK, VTX, BWD, HASH>,                                 \
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,                  \
-                                (int)raster_smem_bytes(VTX));                                 \
+                                (int)raster_smem_bytes(VTX, BWD));                            \
   }                                                                                           \
   cudaError_t prepare_raster_##KK(int* blocks_flat, int* blocks_vtx, int* blocks_bwd) {       \
     cudaError_t e = raster_attr_##KK<false, false, false>();                                  \
@@ -620,7 +640,7 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
                                                       kRasterThreads, raster_smem_bytes(false)); \
     if (e != cudaSuccess) return e;                                                           \
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_bwd, k_raster<KK, false, true, false>, \
-                                                      kRasterThreads, raster_smem_bytes(false)); \
+                                                      kRasterThreads, raster_smem_bytes(false, true)); \
     if (e != cudaSuccess) return e;                                                           \
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_vtx, k_raster<KK, true, false, false>, \
                                                          kRasterThreads, raster_smem_bytes(true)); \
@@ -630,7 +650,7 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
     const size_t sf = raster_smem_bytes(false), sv = raster_smem_bytes(true);                 \
     switch (mode) {                                                                           \
       case 1: k_raster<KK, true, false, false><<<grid, kRasterThreads, sv, st>>>(ws); break;  \
-      case 2: k_raster<KK, false, true, false><<<grid, kRasterThreads, sf, st>>>(ws); break;  \
+      case 2: k_raster<KK, false, true, false><<<grid, kRasterThreads, raster_smem_bytes(false, true), st>>>(ws); break; \
       case 4: k_raster<KK, false, false, true><<<grid, kRasterThreads, sf, st>>>(ws); break;  \
       case 5: k_raster<KK, true, false, true><<<grid, kRasterThreads, sv, st>>>(ws); break;   \
       default: k_raster<KK, false, false, false><<<grid, kRasterThreads, sf, st>>>(ws); break; \
