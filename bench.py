@@ -272,20 +272,22 @@ def differentiable_benchmark(P, torch, steps: int, sorter_k: int = 1):
     """Differentiable compositing on the 1024x1024 layer scene (524,288 quads, flat RGBA):
     each step renders the image, forms dL/dC = 2 (C - T) for the squared L2 distance to a
     target rendered with perturbed colours, and runs the backward (per-quad RGBA
-    gradients, bins and per-pixel order recomputed), all on the device. Reports forward,
-    backward and step times (CUDA events)."""
+    gradients, bins and per-pixel order recomputed; the forward's exact-path mask spares the
+    backward its detection pass), all on the device. Reports forward, backward and step
+    times (CUDA events)."""
     import scenegen
     s = scenegen.config_diff_1024()
     ds = P.DeviceScene.from_scene(s)
     r = P.Renderer(sorter_k=sorter_k)
     tgt = r.render(ds.with_colors(torch.tensor(scenegen.perturbed_target_colors(s.colors, seed=1),
                                                device=ds.colors.device)), s.width, s.height)["rgba"]
-    out = r.make_outputs(s.width, s.height)
+    # the forward also writes its exact-path mask, which spares the backward its detection pass
+    out = r.make_outputs(s.width, s.height, exact_mask=True)
     view = r.view_struct(ds, s.width, s.height, out)
     st = r.render_views([view])                        # sizes the workspace
     frags = int(st.fragments)
     g = torch.zeros_like(out["rgba"])
-    r.render_backward(ds, s.width, s.height, out["rgba"], g)   # sizes it for the backward too
+    r.render_backward(ds, s.width, s.height, out["rgba"], g, exact_mask=out["exact_mask"])
     stream = torch.cuda.current_stream()
     fwd, bwd = [], []
     for i in range(steps + 3):
@@ -294,12 +296,15 @@ def differentiable_benchmark(P, torch, steps: int, sorter_k: int = 1):
         r.render_views([view], check=False)
         g[..., :3] = 2.0 * (out["rgba"][..., :3] - tgt[..., :3])
         e1.record(stream)
-        r.render_backward(ds, s.width, s.height, out["rgba"], g, check=False)
+        r.render_backward(ds, s.width, s.height, out["rgba"], g, check=False, exact_mask=out["exact_mask"])
         e2.record(stream)
         torch.cuda.synchronize()
         if i >= 3:
             fwd.append(e0.elapsed_time(e1))
             bwd.append(e1.elapsed_time(e2))
+    st = P._binding.lr_get_stats(r.ctx, raise_on_error=False)
+    if st.status != 0:
+        raise RuntimeError(f"differentiable benchmark: backward status {st.status}")
     r.close()
     f, b = statistics.median(fwd), statistics.median(bwd)
     return {"workload": "1024x1024, 524,288 quads (layer generator, flat RGBA), loss = squared L2 to a "

@@ -45,7 +45,9 @@ typedef enum {
   LR_ERR_CUDA = -4,          /* a CUDA runtime call failed (see lr_last_error) */
   LR_ERR_TIMEOUT = -5,       /* lr_poll's time limit ran out */
   LR_ERR_OVERFLOW = -6,      /* the workspace's bin-reference capacity was exceeded */
-  LR_ERR_UNSUPPORTED = -7    /* option combination not implemented */
+  LR_ERR_UNSUPPORTED = -7,   /* option combination not implemented */
+  LR_ERR_MASK_MISMATCH = -8  /* lr_render_backward: the exact-path mask given does not
+                                match this scene and context (gradients not valid) */
 } lr_status;
 
 enum { LR_COLOR_FLAT = 0, LR_COLOR_VERTEX = 1 };
@@ -98,6 +100,9 @@ typedef struct {
   uint8_t* rgba8;            /* u8[H][W][4]: rint(clamp(v, 0, 1) * 255) */
   uint32_t* frag_count;      /* u32[H][W]: number of fragments covering the pixel */
   uint64_t* cov_hash;        /* u64[H][W]: sum of splitmix64(2 * quad + triangle) */
+  uint32_t* exact_mask;      /* u32[ceil(H/4)][ceil(W/8)]: per 8x4 half-block, bit ly*8+lx set
+                                if pixel (8 hx + lx, 4 hy + ly) took the exact (overflow) path;
+                                lr_render_backward can take it to skip its own detection */
 } lr_target;
 
 /* One view of a batch: a scene, a camera, a resolution and its outputs. */
@@ -204,12 +209,18 @@ lr_status lr_graph_destroy(lr_graph* graph);
  * grad_out: device f32[H][W][4] = dL/d(R, G, B, A) of the rendered image.
  * fwd_rgba: device f32[H][W][4] = the forward image of the same scene (as lr_render wrote
  *           it); the per-pixel fragment order is recomputed, not stored.
+ * exact_mask: NULL, or the forward's lr_target.exact_mask for this scene rendered on a
+ *           context with the same sorter capacity. Without it the rasteriser streams every
+ *           half-block twice (first to find the pixels the fixed-size sorter cannot order,
+ *           which take the exact path, then with gradients); with it, once. A pixel the
+ *           mask misses makes lr_get_stats report LR_ERR_MASK_MISMATCH, and the gradients
+ *           of that call are not valid (call again without the mask).
  * grad_colors: device f32[Q][4]; gradients are ADDED to it (zero it first).
  * Only LR_COLOR_FLAT scenes (LR_ERR_UNSUPPORTED otherwise). */
 lr_status lr_render_backward(lr_ctx* ctx, const lr_quads* quads, const lr_camera* camera,
                              int32_t width, int32_t height, const float* fwd_rgba,
-                             const float* grad_out, float* grad_colors, void* workspace,
-                             size_t workspace_bytes, lr_stream stream);
+                             const float* grad_out, const uint32_t* exact_mask, float* grad_colors,
+                             void* workspace, size_t workspace_bytes, lr_stream stream);
 
 /* Layout of a workspace of workspace_bytes bytes for this batch (host call). */
 lr_status lr_workspace_layout(const lr_ctx* ctx, int32_t n_views, const lr_view* views,

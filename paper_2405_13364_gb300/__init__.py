@@ -134,9 +134,12 @@ class Renderer:
         return (base + 255) & ~255, self._ws_bytes
 
     # ---- views -----------------------------------------------------------------------------
-    def make_outputs(self, width, height, rgba8=False, count=False, hash=False) -> Outputs:
+    def make_outputs(self, width, height, rgba8=False, count=False, hash=False, exact_mask=False) -> Outputs:
         o = Outputs()
         o["rgba"] = torch.empty((height, width, 4), dtype=torch.float32, device=self.device)
+        if exact_mask:   # one 32-bit word per 8x4 half-block
+            o["exact_mask"] = torch.empty(((height + 3) // 4, (width + 7) // 8), dtype=torch.int32,
+                                          device=self.device)
         if rgba8:
             o["rgba8"] = torch.empty((height, width, 4), dtype=torch.uint8, device=self.device)
         if count:
@@ -148,7 +151,7 @@ class Renderer:
     @staticmethod
     def view_struct(scene: DeviceScene, width: int, height: int, out: Outputs) -> lr_view:
         tgt = lr_target(_ptr(out["rgba"]), _ptr(out.get("rgba8")), _ptr(out.get("count")),
-                        _ptr(out.get("hash")))
+                        _ptr(out.get("hash")), _ptr(out.get("exact_mask")))
         return lr_view(scene.quads_struct(), scene.camera_struct(), width, height, tgt)
 
     def render_views(self, views, stream=None, check: bool = True):
@@ -171,8 +174,8 @@ class Renderer:
         raise LrError(LR_ERR_OVERFLOW, "bin references kept exceeding the workspace")
 
     def render(self, scene: DeviceScene, width: int, height: int, rgba8=False, count=False,
-               hash=False, stream=None, check: bool = True) -> Outputs:
-        out = self.make_outputs(width, height, rgba8, count, hash)
+               hash=False, stream=None, check: bool = True, exact_mask=False) -> Outputs:
+        out = self.make_outputs(width, height, rgba8, count, hash, exact_mask)
         self.render_views([self.view_struct(scene, width, height, out)], stream, check)
         return out
 
@@ -200,8 +203,12 @@ class Renderer:
 
     # ---- differentiation ----------------------------------------------------------------------
     def render_backward(self, scene: DeviceScene, width: int, height: int, fwd_rgba: torch.Tensor,
-                        grad_out: torch.Tensor, stream=None, check: bool = True) -> torch.Tensor:
-        """dL/d(flat per-quad RGBA) given dL/d(image); the fragment order is recomputed."""
+                        grad_out: torch.Tensor, stream=None, check: bool = True,
+                        exact_mask: torch.Tensor | None = None) -> torch.Tensor:
+        """dL/d(flat per-quad RGBA) given dL/d(image); the fragment order is recomputed.
+        exact_mask: the forward's `exact_mask` output (render(..., exact_mask=True)) for the
+        same scene and renderer, which saves the detection pass; if it does not match, the
+        call is repeated without it (with check=True)."""
         stream = torch.cuda.current_stream(self.device) if stream is None else stream
         grad = torch.zeros((scene.num_quads, 4), dtype=torch.float32, device=self.device)
         fwd_rgba = fwd_rgba.contiguous()
@@ -212,11 +219,15 @@ class Renderer:
         for _ in range(3):
             ptr, nbytes = self.workspace(need)
             B.lr_render_backward(self.ctx, scene.quads_struct(), scene.camera_struct(), width, height,
-                                 _ptr(fwd_rgba), _ptr(grad_out), _ptr(grad), ptr, nbytes,
+                                 _ptr(fwd_rgba), _ptr(grad_out), _ptr(exact_mask), _ptr(grad), ptr, nbytes,
                                  stream.cuda_stream)
             if not check:
                 return grad
             st = B.lr_get_stats(self.ctx, raise_on_error=False)
+            if st.status == B.LR_ERR_MASK_MISMATCH:
+                exact_mask = None
+                grad.zero_()
+                continue
             if st.status == LR_ERR_OVERFLOW:
                 need = B.lr_workspace_size_refs(self.ctx, [view], int(st.bin_refs * 1.25) + 1024)
                 grad.zero_()
@@ -347,16 +358,17 @@ class _Composite(torch.autograd.Function):
     @staticmethod
     def forward(actx, colors, renderer, scene, width, height):
         s = scene.with_colors(colors.detach().to(torch.float32).contiguous())
-        out = renderer.render(s, width, height)["rgba"]
+        res = renderer.render(s, width, height, exact_mask=True)
+        out = res["rgba"]
         actx.renderer, actx.scene, actx.size = renderer, s, (width, height)
-        actx.save_for_backward(out)
+        actx.save_for_backward(out, res["exact_mask"])
         return out
 
     @staticmethod
     def backward(actx, grad_out):
-        (out,) = actx.saved_tensors
+        out, mask = actx.saved_tensors
         w, h = actx.size
-        g = actx.renderer.render_backward(actx.scene, w, h, out, grad_out)
+        g = actx.renderer.render_backward(actx.scene, w, h, out, grad_out, exact_mask=mask)
         return g, None, None, None, None
 
 

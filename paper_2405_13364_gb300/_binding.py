@@ -21,10 +21,11 @@ LR_ERR_CUDA = -4
 LR_ERR_TIMEOUT = -5
 LR_ERR_OVERFLOW = -6
 LR_ERR_UNSUPPORTED = -7
+LR_ERR_MASK_MISMATCH = -8
 
 STATUS_NAMES = {0: "LR_OK", 1: "LR_PENDING", -1: "LR_ERR_INVALID_ARG", -2: "LR_ERR_TOO_LARGE",
                 -3: "LR_ERR_OOM", -4: "LR_ERR_CUDA", -5: "LR_ERR_TIMEOUT", -6: "LR_ERR_OVERFLOW",
-                -7: "LR_ERR_UNSUPPORTED"}
+                -7: "LR_ERR_UNSUPPORTED", -8: "LR_ERR_MASK_MISMATCH"}
 
 LR_COLOR_FLAT = 0
 LR_COLOR_VERTEX = 1
@@ -58,7 +59,8 @@ class lr_camera(ctypes.Structure):
 
 class lr_target(ctypes.Structure):
     _fields_ = [("rgba", ctypes.c_void_p), ("rgba8", ctypes.c_void_p),
-                ("frag_count", ctypes.c_void_p), ("cov_hash", ctypes.c_void_p)]
+                ("frag_count", ctypes.c_void_p), ("cov_hash", ctypes.c_void_p),
+                ("exact_mask", ctypes.c_void_p)]
 
 
 class lr_view(ctypes.Structure):
@@ -117,7 +119,7 @@ _SIGNATURES = {
     "lr_render_batch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(lr_view), _P,
                                        ctypes.c_size_t, _P]),
     "lr_render_backward": (ctypes.c_int, [_P, ctypes.POINTER(lr_quads), ctypes.POINTER(lr_camera),
-                                          ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P,
+                                          ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, _P,
                                           ctypes.c_size_t, _P]),
     "lr_workspace_layout": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(lr_view),
                                            ctypes.c_size_t, ctypes.POINTER(lr_ws_layout)]),
@@ -221,11 +223,11 @@ def lr_render_batch(ctx, views, workspace: int, workspace_bytes: int, stream: in
 
 
 def lr_render_backward(ctx, quads: lr_quads, camera: lr_camera, width: int, height: int,
-                       fwd_rgba: int, grad_out: int, grad_colors: int, workspace: int,
+                       fwd_rgba: int, grad_out: int, exact_mask: int, grad_colors: int, workspace: int,
                        workspace_bytes: int, stream: int):
     _check(ctx, load().lr_render_backward(ctx, ctypes.byref(quads), ctypes.byref(camera), width,
-                                          height, fwd_rgba, grad_out, grad_colors, workspace,
-                                          workspace_bytes, stream), "lr_render_backward")
+                                          height, fwd_rgba, grad_out, exact_mask, grad_colors,
+                                          workspace, workspace_bytes, stream), "lr_render_backward")
 
 
 def lr_workspace_layout(ctx, views, workspace_bytes: int) -> lr_ws_layout:

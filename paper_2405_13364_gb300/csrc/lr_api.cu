@@ -288,7 +288,7 @@ static lr_status check_view(lr_ctx* c, const lr_view& v) {
   }
   if (!v.target.rgba || !aligned(v.target.rgba, 16)) return fail(c, LR_ERR_INVALID_ARG, "rgba output must be non-null and 16-byte aligned%s");
   if ((v.target.rgba8 && !aligned(v.target.rgba8, 4)) || (v.target.frag_count && !aligned(v.target.frag_count, 4)) ||
-      (v.target.cov_hash && !aligned(v.target.cov_hash, 8)))
+      (v.target.cov_hash && !aligned(v.target.cov_hash, 8)) || (v.target.exact_mask && !aligned(v.target.exact_mask, 4)))
     return fail(c, LR_ERR_INVALID_ARG, "misaligned optional output%s");
   const float n = v.camera.near_z, f = v.camera.far_z;
   if (!(n > 0.0f) || !(f >= n) || !(f < 3.4e38f)) return fail(c, LR_ERR_INVALID_ARG, "need 0 < near <= far < inf%s");
@@ -368,6 +368,7 @@ struct BwdArgs {
   const float* fwd;
   const float* grad_out;
   float* grad_colors;
+  const uint32_t* exact_mask;
 };
 
 // A render, checked and laid out on the host: workspace pointers and view descriptors.
@@ -398,6 +399,7 @@ static void describe_views(int32_t n_views, const lr_view* views, std::vector<Vi
     d.out8 = v.target.rgba8;
     d.cnt = v.target.frag_count;
     d.hash = reinterpret_cast<unsigned long long*>(v.target.cov_hash);
+    d.xmask = v.target.exact_mask;
     const float* M = v.camera.view_proj;
     for (int k = 0; k < 4; ++k) {
       d.m[k] = M[k];
@@ -456,6 +458,7 @@ static lr_status launch_sequence(lr_ctx* ctx, const Prepared& P, cudaStream_t st
     ws.fwd = bwd->fwd;
     ws.grad_out = bwd->grad_out;
     ws.grad_col = bwd->grad_colors;
+    ws.bwd_mask = bwd->exact_mask;
   }
   const int n_views = ws.n_views;
   rec(ctx, timed, 0, st);
@@ -636,8 +639,9 @@ extern "C" lr_status lr_render_batch(lr_ctx* ctx, int32_t n_views, const lr_view
 
 extern "C" lr_status lr_render_backward(lr_ctx* ctx, const lr_quads* quads, const lr_camera* camera,
                                         int32_t width, int32_t height, const float* fwd_rgba,
-                                        const float* grad_out, float* grad_colors, void* workspace,
-                                        size_t workspace_bytes, lr_stream stream) {
+                                        const float* grad_out, const uint32_t* exact_mask,
+                                        float* grad_colors, void* workspace, size_t workspace_bytes,
+                                        lr_stream stream) {
   if (!ctx) return LR_ERR_INVALID_ARG;
   if (!quads || !camera || !fwd_rgba || !grad_out || !grad_colors)
     return fail(ctx, LR_ERR_INVALID_ARG, "null argument%s");
@@ -652,7 +656,8 @@ extern "C" lr_status lr_render_backward(lr_ctx* ctx, const lr_quads* quads, cons
   v.width = width;
   v.height = height;
   v.target.rgba = const_cast<float*>(fwd_rgba);   // not written by the backward pass
-  BwdArgs b{fwd_rgba, grad_out, grad_colors};
+  if (exact_mask && !aligned(exact_mask, 4)) return fail(ctx, LR_ERR_INVALID_ARG, "exact_mask must be 4-byte aligned%s");
+  BwdArgs b{fwd_rgba, grad_out, grad_colors, exact_mask};
   return enqueue(ctx, 1, &v, workspace, workspace_bytes, stream, &b);
 }
 

@@ -61,6 +61,7 @@ struct ViewDev {
   uint8_t* out8;             // optional
   uint32_t* cnt;             // optional
   unsigned long long* hash;  // optional
+  uint32_t* xmask;           // optional: exact-path bits per 8x4 half-block
   float m[12];               // rows 0, 1, 3 of the view-projection (x, y, w)
   float near_z, far_z;
   float half_w, half_h;
@@ -149,6 +150,7 @@ struct Ws {
   const float* grad_out;     // f32[H][W][4] of view 0
   const float* fwd;          // f32[H][W][4] of view 0
   float* grad_col;           // f32[Q][4] of view 0
+  const uint32_t* bwd_mask;  // optional: the forward's exact-path mask of view 0
 };
 
 // 32x32 bit-matrix transpose across a warp: lane r holds row r on entry (bit c = element

@@ -313,7 +313,7 @@ struct PixelState {
       const float om = 1.0f - col.w;
       float da = gp.gr * T * col.x + gp.gg * T * col.y + gp.gb * T * col.z;
       if (om > 1e-6f) {
-        const float inv = 1.0f / om;
+        const float inv = rcp_approx(om);   // gradients need no correctly rounded divide
         da -= (gp.gr * (gp.fr - r) + gp.gg * (gp.fg - g) + gp.gb * (gp.fb - b)) * inv;
         da += gp.ga * gp.fT * inv;
       }
@@ -571,8 +571,16 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
     // The backward pass streams the half-block twice: first without gradients, to learn
     // which pixels the sorter cannot order (those are left to the exact path, which
     // emits their whole gradient), then with gradients for the other pixels only.
+    // With the forward's exact-path mask the detection pass is skipped.
     bool pre_flagged = false;
-    for (int pass = BWD ? 0 : 1; pass < 2; ++pass) {
+    int first_pass = BWD ? 0 : 1;
+    if (BWD && ws.bwd_mask) {
+      const uint32_t hbx = (uint32_t)ox / kHbW, hby = (uint32_t)oy / kHbH;
+      const uint32_t hbw = ((uint32_t)V.width + kHbW - 1) / kHbW;
+      pre_flagged = (ws.bwd_mask[hby * hbw + hbx] >> lane) & 1u;
+      first_pass = 1;
+    }
+    for (int pass = first_pass; pass < 2; ++pass) {
     if (BWD) {
       st.init();
       st.flagged = pre_flagged;
@@ -596,6 +604,15 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
     }
 
     // ---- finish the half-block ---------------------------------------------------------
+    // a pixel the given mask missed has had part of its gradient added already: report it
+    if (BWD && ws.bwd_mask && st.flagged && !pre_flagged) set_error(ws.ctrl, LR_ERR_MASK_MISMATCH);
+    if (!BWD && V.xmask) {
+      const uint32_t fm = __ballot_sync(0xffffffffu, pix_ok && st.flagged);
+      if (lane == 0) {
+        const uint32_t hbw = ((uint32_t)V.width + kHbW - 1) / kHbW;
+        V.xmask[((uint32_t)oy / kHbH) * hbw + (uint32_t)ox / kHbW] = fm;
+      }
+    }
     if (!st.flagged) st.flush(V);
     if (pix_ok) {
       const long long pidx = (long long)py * V.width + px;

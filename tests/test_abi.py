@@ -51,8 +51,8 @@ def test_struct_sizes_match_header_layout(lib):
     assert ctypes.sizeof(B.lr_config) == 7 * 4
     assert ctypes.sizeof(B.lr_quads) == 6 * 8
     assert ctypes.sizeof(B.lr_camera) == 18 * 4
-    assert ctypes.sizeof(B.lr_target) == 4 * 8
-    assert ctypes.sizeof(B.lr_view) == 48 + 72 + 8 + 32
+    assert ctypes.sizeof(B.lr_target) == 5 * 8
+    assert ctypes.sizeof(B.lr_view) == 48 + 72 + 8 + 40
 
 
 def test_host_side_argument_errors(lib):
@@ -64,7 +64,7 @@ def test_host_side_argument_errors(lib):
     assert lib.lr_workspace_size(None, 10, 64, 64, ctypes.byref(n)) == B.LR_ERR_INVALID_ARG
     assert lib.lr_get_stats(None, None) == B.LR_ERR_INVALID_ARG
     assert lib.lr_render(None, None, None, 1, 1, None, None, 0, None) == B.LR_ERR_INVALID_ARG
-    assert lib.lr_render_backward(None, None, None, 1, 1, None, None, None, None, 0, None) == \
+    assert lib.lr_render_backward(None, None, None, 1, 1, None, None, None, None, None, 0, None) == \
         B.LR_ERR_INVALID_ARG
 
 
