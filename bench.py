@@ -42,9 +42,10 @@ LAUNCHES_PER_FRAME = 10
 # (workload, K, carried colours), with the hash of the rasteriser sources they were taken
 # on: the figure is reported only while the kernel is unchanged.
 RASTER_TRAFFIC = {
-    # (DRAM read + write bytes per launch, ncu smsp__issue_active, source hash)
-    ("layers", 1, False): (102_366_208, 0.768, "9db22f6ee77ee52b"),     # profiles/k_raster_layers1080p.md
-    ("particles", 1, False): (390_256_640, 0.724, "9db22f6ee77ee52b"),  # profiles/k_raster_particles1080p.md
+    # (DRAM read + write bytes per launch, ncu smsp__issue_active, ncu smsp__inst_executed,
+    #  source hash of the captured build)
+    ("layers", 1, False): (102_366_208, 0.768, 463_965_615, "9db22f6ee77ee52b"),      # profiles/k_raster_layers1080p.md
+    ("particles", 1, False): (390_256_640, 0.724, 1_065_570_390, "9db22f6ee77ee52b"),  # profiles/k_raster_particles1080p.md
 }
 RASTER_SOURCES = ("lr_raster.cuh", "lr_common.cuh")
 LANES_PER_SM_CLK = 128
@@ -98,12 +99,12 @@ def raster_source_hash() -> str:
 
 
 def raster_capture(workload: str, k: int, carry: bool):
-    """(traffic bytes, issue-slot utilisation) of the committed ncu capture of this
-    rasteriser build, or (None, None) once the sources differ from the captured build."""
+    """(traffic bytes, issue-slot utilisation, warp instructions) of the committed ncu
+    capture of this rasteriser build, or Nones once the sources differ from it."""
     t = RASTER_TRAFFIC.get((workload, k, carry))
-    if t is None or t[2] != raster_source_hash():
-        return None, None
-    return t[0], t[1]
+    if t is None or t[3] != raster_source_hash():
+        return None, None, None
+    return t[0], t[1], t[2]
 
 
 class ClockSampler:
@@ -491,6 +492,27 @@ def run_gpu(args):
     peak = SM_COUNT * LANES_PER_SM_CLK * sm_max * 1e6 / 1e12   # T lane-ops/s
     achieved = ops / (raster_ms * 1e-3) / 1e12
     peaks = _measured_peaks()
+    # the rasteriser's instruction-issue ceiling: every scheduler issuing one warp
+    # instruction per clock, at the captured build's warp instructions per fragment
+    issue_ceiling = None
+    inst = raster_capture(args.workload, args.k, carry)[2]
+    if inst:
+        ceil_gfrag = SM_COUNT * 4 * sm_max * 1e6 / (inst / frags) / 1e9
+        got = frags / (raster_ms * 1e-3) / 1e9
+        issue_ceiling = {"warp_instructions_per_fragment": round(inst / frags, 3),
+                         "ceiling_gfrag_s": round(ceil_gfrag, 1), "achieved_gfrag_s": round(got, 1),
+                         "frac": round(got / ceil_gfrag, 4)}
+
+    # pixels that needed the exact path, per sorter capacity (the paper's Sec. 3 error rates
+    # are for pixels left misordered; here they are recomputed exactly)
+    overflow_frac = {}
+    if world == 1:
+        for kk in (1, 3, 8, 12):
+            rk = P.Renderer(sorter_k=kk)
+            ok_ = rk.make_outputs(W, H)
+            stk = rk.render_views([rk.view_struct(ds, W, H, ok_)])
+            overflow_frac[f"k{kk}"] = round(int(stk.overflow_pixels) / (W * H), 6)
+            rk.close()
 
     # ---- CPU oracle on a bounded sample: full frames for ~10 s ---------------------------
     cpu = None
@@ -505,6 +527,13 @@ def run_gpu(args):
         dt = time.perf_counter() - t0
         cpu = {"value": round(cfrags / dt / 1e9, 4), "unit": "Gfrag/s", "cores": cores, "kind": "oracle",
                "sample": f"{n_frames} full 1920x1080 frames ({dt:.1f} s)"}
+        small = scenegen.config_small_frustum()
+        t1 = []
+        for _ in range(3):
+            a = time.perf_counter()
+            oracle.render(small, nthreads=1)
+            t1.append(time.perf_counter() - a)
+        cpu["small_frustum_single_thread_ms"] = round(1e3 * statistics.median(t1), 2)
 
     line = {
         "metric": METRIC if args.workload == "layers" else f"Gfrag/s ({args.workload})",
@@ -526,8 +555,11 @@ def run_gpu(args):
                      "traffic": raster_capture(args.workload, args.k, carry)[0],
                      "ncu_issue_active": raster_capture(args.workload, args.k, carry)[1],
                      "ops_per_fragment": OPS_PER_FRAG_BASE + args.k,
-                     "peak_basis": f"{SM_COUNT} SMs x 128 lanes x {sm_max:.0f} MHz (max SM clock)"},
+                     "peak_basis": f"{SM_COUNT} SMs x 128 lanes x {sm_max:.0f} MHz (max SM clock)",
+                     "issue_ceiling": issue_ceiling},
         "setup_hbm": None,
+        "binning_hbm": None,
+        "overflow_pixel_fraction": overflow_frac,
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 3), "unit": "Gfrag/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4),
@@ -542,11 +574,21 @@ def run_gpu(args):
         line["measured_peaks"] = {"hbm_gbs": peaks.get("hbm_gbs")}
         # setup is HBM-bound: algorithmic bytes = 16 B indices + 12 B per vertex (each vertex
         # read once, shared) + 80 B of records written per quad
-        setup_bytes = 16 * scene.num_quads + 12 * scene.num_vertices + 80 * scene.num_quads
+        setup_bytes = (16 * scene.num_quads if scene.indices is not None else 0) + 12 * scene.num_vertices + \
+            80 * scene.num_quads
         if stages.get("setup"):
             gbs = setup_bytes / (stages["setup"] * 1e-3) / 1e9
             line["setup_hbm"] = {"achieved_gbs": round(gbs, 1), "peak_gbs": peaks.get("hbm_gbs"),
                                  "frac": round(gbs / peaks["hbm_gbs"], 4), "bytes": setup_bytes}
+        # binning (count + scan + scatter): 12 B of box and flags read per quad by the count,
+        # 16 B (box, flags, representative depth) by the scatter, 8 B written per reference,
+        # 16 B per bin (count, offset, cursor, order)
+        bin_bytes = 28 * scene.num_quads + 8 * int(st0["bin_refs"]) + 16 * ((W + 31) // 32) * ((H + 31) // 32)
+        bin_ms = stages.get("count", 0) + stages.get("scan", 0) + stages.get("scatter", 0)
+        if bin_ms:
+            gbs = bin_bytes / (bin_ms * 1e-3) / 1e9
+            line["binning_hbm"] = {"achieved_gbs": round(gbs, 1), "peak_gbs": peaks.get("hbm_gbs"),
+                                   "frac": round(gbs / peaks["hbm_gbs"], 4), "bytes": bin_bytes}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
