@@ -1,8 +1,8 @@
 // lr_api.cu -- the C ABI (include/lr.h): argument checking, workspace layout, and the
 // launch sequence of one render:
 //
-//   k_write_views  view descriptors -> workspace (kernel parameters, no host buffer)
-//   k_init         zero control block and bin counters
+//   k_init         zero control block and bin counters; view descriptors -> workspace
+//                  (kernel parameters, no host buffer; k_write_views for views past 16)
 //   k_setup        Stage 1  (Sec. 2, "Stage 1: quad setup")
 //   k_bin_count    Stage 2, Phase 1
 //   k_bin_scan     Stage 2, Phase 2
@@ -25,7 +25,7 @@
 #include "lr_serve.h"
 
 namespace lr {
-__global__ void k_init(Ws ws, unsigned long long refs_cap);
+__global__ void k_init(Ws ws, unsigned long long refs_cap, ViewChunk views, ViewDev* views_dst);
 __global__ void k_setup(Ws ws);
 __global__ void k_bin_count(Ws ws);
 __global__ void k_bin_scan(Ws ws);
@@ -45,12 +45,6 @@ LR_DECLARE_RASTER(4)
 LR_DECLARE_RASTER(6)
 LR_DECLARE_RASTER(8)
 LR_DECLARE_RASTER(12)
-
-constexpr int kViewsPerLaunch = 16;
-struct ViewChunk {
-  ViewDev v[kViewsPerLaunch];
-  int first, count;
-};
 
 __global__ void k_write_views(ViewChunk chunk, ViewDev* dst) {
   const int i = threadIdx.x;
@@ -462,20 +456,26 @@ static lr_status launch_sequence(lr_ctx* ctx, const Prepared& P, cudaStream_t st
   }
   const int n_views = ws.n_views;
   rec(ctx, timed, 0, st);
+  // the first kViewsPerLaunch descriptors travel with k_init, further ones with k_write_views
+  ViewChunk chunk;
+  memset(&chunk, 0, sizeof(chunk));
   if (staging) {
     cudaError_t e = cudaMemcpyAsync(P.views_dev, staging, sizeof(ViewDev) * (size_t)n_views, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "view descriptor copy");
   } else {
-    for (int first = 0; first < n_views; first += kViewsPerLaunch) {
-      ViewChunk chunk;
-      memset(&chunk, 0, sizeof(chunk));
-      chunk.first = first;
-      chunk.count = std::min(kViewsPerLaunch, n_views - first);
-      for (int i = 0; i < chunk.count; ++i) chunk.v[i] = P.vd[first + i];
-      k_write_views<<<1, 32, 0, st>>>(chunk, P.views_dev);
+    chunk.count = std::min(kViewsPerLaunch, n_views);
+    for (int i = 0; i < chunk.count; ++i) chunk.v[i] = P.vd[i];
+    for (int first = kViewsPerLaunch; first < n_views; first += kViewsPerLaunch) {
+      ViewChunk more;
+      memset(&more, 0, sizeof(more));
+      more.first = first;
+      more.count = std::min(kViewsPerLaunch, n_views - first);
+      for (int i = 0; i < more.count; ++i) more.v[i] = P.vd[first + i];
+      k_write_views<<<1, 32, 0, st>>>(more, P.views_dev);
     }
   }
-  k_init<<<std::max(1, (L.total_bins + 255) / 256), 256, 0, st>>>(ws, (unsigned long long)L.refs_cap);
+  k_init<<<std::max(1, (L.total_bins + 255) / 256), 256, 0, st>>>(ws, (unsigned long long)L.refs_cap, chunk,
+                                                                  P.views_dev);
   if (L.total_quads > 0) k_setup<<<(unsigned)((L.total_quads + 255) / 256), 256, 0, st>>>(ws);
   rec(ctx, timed, 1, st);
   if (L.total_chunks > 0) k_bin_count<<<L.total_chunks, kBinThreads, 0, st>>>(ws);
@@ -689,8 +689,13 @@ extern "C" lr_status lr_get_stats(lr_ctx* ctx, lr_stats* stats) {
     stats->status = h.error;
     stats->n_views = ctx->last_views;
     stats->quads_in = ctx->last_quads;
-    stats->quads_visible = (int64_t)h.visible;
-    for (int i = 0; i < 8; ++i) stats->culled[i] = (int64_t)h.culled[i];
+    // k_setup counts culled quads only; every other input quad is visible
+    int64_t culled = 0;
+    for (int i = 0; i < 8; ++i) {
+      stats->culled[i] = (int64_t)h.culled[i];
+      culled += stats->culled[i];
+    }
+    stats->quads_visible = ctx->last_quads - culled;
     stats->bin_refs = (int64_t)h.refs_total;
     stats->bin_refs_capacity = ctx->last_cap;
     stats->bins_nonempty = (int64_t)h.bins_nonempty;

@@ -76,6 +76,14 @@ struct ViewDev {
   int chunk_base;            // first binning chunk (kChunkQuads quads) of this view
 };
 
+// Up to kViewsPerLaunch view descriptors passed by value to a kernel, which writes them to
+// the workspace (no host buffer is needed).
+constexpr int kViewsPerLaunch = 16;
+struct ViewChunk {
+  ViewDev v[kViewsPerLaunch];
+  int first, count;
+};
+
 // Device control block at the start of the workspace.
 struct Ctrl {
   int error;                         // first error (lr_status), 0 = none
@@ -88,7 +96,7 @@ struct Ctrl {
   unsigned long long ovf_head;
   unsigned long long sort_head;      // k_bin_sort_big's queue over the high-density bins
   unsigned long long fragments;
-  unsigned long long visible;
+  unsigned long long unused0;
   unsigned long long culled[8];
   unsigned long long bins_nonempty;
   unsigned long long bins_high;
@@ -274,25 +282,53 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
   return z ^ (z >> 31);
 }
 
+// Approximate reciprocal (PTX rcp.approx.ftz.f32, about 1 ulp): colours, gradients and
+// sort hints only, never coverage or the depth key.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // Representative depth of a quad over a pixel box: the plane of one triangle evaluated (in
 // plain fp32, approximately) at the box centre, clamped to the range of the quad's vertex
 // 1/w. Only the order quality of stage 1 (the per-bin depth sort) depends on it; exactness
-// is restored by the per-pixel sorter and the overflow path.
+// is restored by the per-pixel sorter and the overflow path. The triangle's vertices are
+// picked with selects, so the arrays stay in registers.
 __device__ __forceinline__ float rep_depth_of(const int X[4], const int Y[4], const float Q[4], uint32_t info,
                                               int x0, int x1, int y0, int y1) {
-  const float Xs[4] = {(float)X[0], (float)X[1], (float)X[2], (float)X[3]};
-  const float Ys[4] = {(float)Y[0], (float)Y[1], (float)Y[2], (float)Y[3]};
+  const bool t0 = (info & kInfoTri0) != 0;   // triangle (v0 v1 v2), else (v0 v2 v3)
+  const float xa = (float)X[0], ya = (float)Y[0], qa = Q[0];
+  const float xb = (float)(t0 ? X[1] : X[2]), yb = (float)(t0 ? Y[1] : Y[2]), qb = t0 ? Q[1] : Q[2];
+  const float xc = (float)(t0 ? X[2] : X[3]), yc = (float)(t0 ? Y[2] : Y[3]), qc = t0 ? Q[2] : Q[3];
   const float qmin = fminf(fminf(Q[0], Q[1]), fminf(Q[2], Q[3]));
   const float qmax = fmaxf(fmaxf(Q[0], Q[1]), fmaxf(Q[2], Q[3]));
-  const int i1 = (info & kInfoTri0) ? 1 : 2, i2 = (info & kInfoTri0) ? 2 : 3;
   const float px = 128.0f * (float)(x0 + x1) + 128.0f, py = 128.0f * (float)(y0 + y1) + 128.0f;
-  const float A = (Xs[i1] - Xs[0]) * (Ys[i2] - Ys[0]) - (Ys[i1] - Ys[0]) * (Xs[i2] - Xs[0]);
+  const float A = (xb - xa) * (yc - ya) - (yb - ya) * (xc - xa);
   if (!(fabsf(A) > 0.0f)) return qmax;
-  const float l1 = ((Xs[0] - Xs[i2]) * (py - Ys[i2]) - (Ys[0] - Ys[i2]) * (px - Xs[i2])) / A;
-  const float l2 = ((Xs[i1] - Xs[0]) * (py - Ys[0]) - (Ys[i1] - Ys[0]) * (px - Xs[0])) / A;
-  float r = Q[0] + l1 * (Q[i1] - Q[0]) + l2 * (Q[i2] - Q[0]);
+  const float iA = rcp_approx(A);
+  const float l1 = ((xa - xc) * (py - yc) - (ya - yc) * (px - xc)) * iA;
+  const float l2 = ((xb - xa) * (py - ya) - (yb - ya) * (px - xa)) * iA;
+  float r = qa + l1 * (qb - qa) + l2 * (qc - qa);
   r = fminf(fmaxf(r, qmin), qmax);
   return r > 0.0f ? r : qmin;
+}
+
+// Correctly rounded quotient a / w given y = 1/w rounded to nearest, by Markstein's
+// correction (P. Markstein, "Computation of elementary functions on the IBM RISC System/6000
+// processor", IBM J. Res. Dev. 34(1), 1990): if y is the correctly rounded reciprocal and q
+// is within one ulp of a/w, then q + r y with the residual r = a - w q (exact in one fused
+// multiply-add) rounds once to the correctly rounded quotient. q = a y can be two ulps off,
+// so a first correction brings it within one ulp and a second one rounds it correctly. The
+// theorem needs every operand, residual and the quotient to be normal numbers; anything
+// outside the range tested below takes the IEEE division.
+__device__ __forceinline__ float div_rn_by(float a, float w, float y) {
+  const float q0 = __fmul_rn(a, y);
+  const float aa = fabsf(a);
+  if (!(w >= 0x1p-60f && w <= 0x1p60f && aa >= 0x1p-90f && aa <= 0x1p60f && fabsf(q0) >= 0x1p-60f))
+    return __fdiv_rn(a, w);
+  const float q1 = __fmaf_rn(__fmaf_rn(-q0, w, a), y, q0);
+  return __fmaf_rn(__fmaf_rn(-q1, w, a), y, q1);
 }
 
 }  // namespace lr

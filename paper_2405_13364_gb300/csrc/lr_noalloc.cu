@@ -28,7 +28,7 @@
 #include "lr_raster.cuh"
 
 namespace lr {
-__global__ void k_init(Ws ws, unsigned long long refs_cap);
+__global__ void k_init(Ws ws, unsigned long long refs_cap, ViewChunk views, ViewDev* views_dst);
 __global__ void k_setup(Ws ws);
 __global__ void k_bin_count(Ws ws);
 __global__ void k_bin_scan(Ws ws);
@@ -195,7 +195,9 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int chunks = (int)((Q + kChunkQuads - 1) / kChunkQuads);
   k_noalloc_view<<<1, 1, 0, st>>>(v, reinterpret_cast<ViewDev*>(base + o_view));
-  k_init<<<(int)((nbins + 255) / 256), 256, 0, st>>>(ws, (unsigned long long)cap);
+  ViewChunk no_views;
+  memset(&no_views, 0, sizeof(no_views));
+  k_init<<<(int)((nbins + 255) / 256), 256, 0, st>>>(ws, (unsigned long long)cap, no_views, nullptr);
   if (Q > 0) k_setup<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(ws);
   if (chunks > 0) k_bin_count<<<chunks, kBinThreads, 0, st>>>(ws);
   k_bin_scan<<<1, 1024, 0, st>>>(ws);

@@ -249,12 +249,6 @@ static __device__ __noinline__ uint32_t tri_mask_slow(const TriSm& T, int ox, in
   return mask;
 }
 
-// Approximate reciprocal (PTX rcp.approx.ftz.f32, about 1 ulp), for colours only.
-__device__ __forceinline__ float rcp_approx(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
 
 // Exact depth key (interpolated 1/w, Sec. 2 "Stage 3", the reading O.8 of the depth
 // formula) of a triangle record at pixel (px, py) = (ox + lx, oy + ly) of its half-block;

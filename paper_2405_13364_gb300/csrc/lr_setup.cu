@@ -8,9 +8,10 @@
 // skip them with one 8-byte load.
 //
 // Exact arithmetic: every fp32 operation that decides coverage or depth order uses the
-// explicitly rounded intrinsics (__fmul_rn, __fadd_rn, __fdiv_rn), which are never fused
-// into multiply-adds, so the results are bit-identical to any IEEE implementation that
-// evaluates the same operations in the same order:
+// explicitly rounded intrinsics (__fmul_rn, __fadd_rn, __frcp_rn), which are never fused
+// into multiply-adds, and the two quotients by w are correctly rounded (div_rn_by), so the
+// results are bit-identical to any IEEE implementation that evaluates the same operations
+// in the same order:
 //   c_r  = ((M[r][0] x + M[r][1] y) + M[r][2] z) + M[r][3]        (rows x, y, w)
 //   sx   = ((cx / w) + 1) * (W / 2),  sy = (1 - (cy / w)) * (H / 2)
 //   X    = rint(sx * 256) (8 fractional bits, round half to even),  q = 1 / w
@@ -22,9 +23,11 @@
 
 namespace lr {
 
-// Zeroes the control block and the bin counters. Launched with block 0 covering the
-// whole control block, so the final store of refs_cap is ordered after its zeroing.
-__global__ void k_init(Ws ws, unsigned long long refs_cap) {
+// Zeroes the control block and the bin counters and writes the first views' descriptors.
+// Launched with block 0 covering the whole control block, so the final store of refs_cap is
+// ordered after its zeroing.
+__global__ void k_init(Ws ws, unsigned long long refs_cap, ViewChunk views, ViewDev* views_dst) {
+  if (blockIdx.x == 0 && threadIdx.x < views.count) views_dst[views.first + threadIdx.x] = views.v[threadIdx.x];
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
   if (i < (long long)(sizeof(Ctrl) / 4)) reinterpret_cast<uint32_t*>(ws.ctrl)[i] = 0u;
@@ -86,14 +89,17 @@ __global__ __launch_bounds__(256) void k_setup(Ws ws) {
       } else if (!(w >= V.near_z && w <= V.far_z)) {
         why = kDepth;
       } else {
-        const float sx = __fmul_rn(__fadd_rn(__fdiv_rn(cx, w), 1.0f), V.half_w);
-        const float sy = __fmul_rn(__fsub_rn(1.0f, __fdiv_rn(cy, w)), V.half_h);
+        // q = 1/w correctly rounded; cx / w and cy / w from it by a correction that gives
+        // the correctly rounded quotient (div_rn_by)
+        const float qk = __frcp_rn(w);
+        const float sx = __fmul_rn(__fadd_rn(div_rn_by(cx, w, qk), 1.0f), V.half_w);
+        const float sy = __fmul_rn(__fsub_rn(1.0f, div_rn_by(cy, w, qk)), V.half_h);
         if (!(fabsf(sx) <= kGuardPx && fabsf(sy) <= kGuardPx)) {
           why = kGuard;
         } else {
           X[k] = __float2int_rn(__fmul_rn(sx, 256.0f));
           Y[k] = __float2int_rn(__fmul_rn(sy, 256.0f));
-          q[k] = __fdiv_rn(1.0f, w);
+          q[k] = qk;
         }
       }
       if (why != kVisible && (worst == kVisible || why < worst)) worst = why;
@@ -122,7 +128,7 @@ __global__ __launch_bounds__(256) void k_setup(Ws ws) {
             info |= kInfoSwap0 << t;
             A = -A;
           }
-          const float it = __fdiv_rn(1.0f, __ll2float_rn(A));
+          const float it = __frcp_rn(__ll2float_rn(A));
           if (t) inv.y = it; else inv.x = it;
           const int xb = t ? X[2] : X[1], yb = t ? Y[2] : Y[1], xc = t ? X[3] : X[2], yc = t ? Y[3] : Y[2];
           const long long wx = (long long)max(X[0], max(xb, xc)) - min(X[0], min(xb, xc));
@@ -164,13 +170,12 @@ __global__ __launch_bounds__(256) void k_setup(Ws ws) {
     ws.rec_rep[g] = rep;
     if (bad) set_error(ws.ctrl, LR_ERR_INVALID_ARG);
   }
-  // per-warp statistics: one atomic per reason present in the warp
-  const unsigned act = __ballot_sync(0xffffffffu, active);
-  for (uint32_t r = 0; r <= kNoPixel; ++r) {
-    const unsigned m = __ballot_sync(0xffffffffu, active && reason == r) & act;
-    if (m && (threadIdx.x & 31) == 0) {
-      if (r == kVisible) atomicAdd(&ws.ctrl->visible, (unsigned long long)__popc(m));
-      else atomicAdd(&ws.ctrl->culled[r], (unsigned long long)__popc(m));
+  // statistics: culled quads per reason, one atomic per reason present in the warp (the
+  // host derives the visible count, so warps without a culled quad issue no atomic)
+  if (__ballot_sync(0xffffffffu, active && reason != kVisible)) {
+    for (uint32_t r = kVisible + 1; r <= kNoPixel; ++r) {
+      const unsigned m = __ballot_sync(0xffffffffu, active && reason == r);
+      if (m && (threadIdx.x & 31) == 0) atomicAdd(&ws.ctrl->culled[r], (unsigned long long)__popc(m));
     }
   }
 }
