@@ -19,32 +19,42 @@
 namespace lr {
 
 // Exact fragment of record rec, triangle t at pixel (px, py): returns false if the pixel
-// centre is not covered; otherwise the sort key and straight RGBA colour.
-__device__ bool frag_eval(const Ws& ws, const ViewDev& V, uint32_t rec, int t, int px, int py,
-                          unsigned long long* sk, float4* col) {
+// centre is not covered; otherwise the sort key and (if col) the straight RGBA colour.
+// The triangle's vertices are picked with selects, so the record stays in registers.
+__device__ __forceinline__ bool frag_eval(const Ws& ws, const ViewDev& V, uint32_t rec, int t, int px, int py,
+                                          unsigned long long& sk, float4* col) {
   const QuadRec R = load_rec(ws.rec, rec);
   if (!(R.info & (t ? kInfoTri1 : kInfoTri0))) return false;
-  int ia = 0, ib = t ? 2 : 1, ic = t ? 3 : 2;
-  if (R.info & (kInfoSwap0 << t)) { const int tmp = ib; ib = ic; ic = tmp; }
-  const int vi[3] = {ia, ib, ic};
+  // triangle t = (v0, v[1 + t], v[2 + t]); a negative area swaps its last two vertices
+  const bool sw = (R.info & (kInfoSwap0 << t)) != 0;
+  const int ib = sw ? 2 + t : 1 + t, ic = sw ? 1 + t : 2 + t;
+  const int xa = R.X[0], ya = R.Y[0];
+  const int xb = ib == 1 ? R.X[1] : (ib == 2 ? R.X[2] : R.X[3]);
+  const int yb = ib == 1 ? R.Y[1] : (ib == 2 ? R.Y[2] : R.Y[3]);
+  const int xc = ic == 1 ? R.X[1] : (ic == 2 ? R.X[2] : R.X[3]);
+  const int yc = ic == 1 ? R.Y[1] : (ic == 2 ? R.Y[2] : R.Y[3]);
   const long long Px = 256LL * px + 128, Py = 256LL * py + 128;
+  // edge functions e0 = E(b -> c), e1 = E(c -> a), e2 = E(a -> b); top-left rule
   long long e[3];
+  {
+    const int ux[3] = {xb, xc, xa}, uy[3] = {yb, yc, ya}, wx[3] = {xc, xa, xb}, wy[3] = {yc, ya, yb};
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const int u = vi[k == 0 ? 1 : (k == 1 ? 2 : 0)];
-    const int w = vi[k == 0 ? 2 : (k == 1 ? 0 : 1)];
-    const long long dx = (long long)R.X[w] - R.X[u], dy = (long long)R.Y[w] - R.Y[u];
-    e[k] = dx * (Py - R.Y[u]) - dy * (Px - R.X[u]);
-    const bool owned = dy < 0 || (dy == 0 && dx > 0);
-    if (!(e[k] > 0 || (e[k] == 0 && owned))) return false;
+    for (int k = 0; k < 3; ++k) {
+      const long long dx = (long long)wx[k] - ux[k], dy = (long long)wy[k] - uy[k];
+      e[k] = dx * (Py - uy[k]) - dy * (Px - ux[k]);
+      const bool owned = dy < 0 || (dy == 0 && dx > 0);
+      if (!(e[k] > 0 || (e[k] == 0 && owned))) return false;
+    }
   }
-  const float inv = R.inv[t];
+  const float inv = t ? R.inv[1] : R.inv[0];
+  const float qa = R.q[0];
+  const float qb = ib == 1 ? R.q[1] : (ib == 2 ? R.q[2] : R.q[3]);
+  const float qc = ic == 1 ? R.q[1] : (ic == 2 ? R.q[2] : R.q[3]);
   const float l1 = __fmul_rn(__ll2float_rn(e[1]), inv);
   const float l2 = __fmul_rn(__ll2float_rn(e[2]), inv);
-  const float key = __fadd_rn(R.q[ia], __fadd_rn(__fmul_rn(l1, __fsub_rn(R.q[ib], R.q[ia])),
-                                                  __fmul_rn(l2, __fsub_rn(R.q[ic], R.q[ia]))));
+  const float key = __fadd_rn(qa, __fadd_rn(__fmul_rn(l1, __fsub_rn(qb, qa)), __fmul_rn(l2, __fsub_rn(qc, qa))));
   const uint32_t jl = (uint32_t)(rec - V.quad_base);
-  *sk = ((unsigned long long)__float_as_uint(key) << 32) | (2u * jl + (uint32_t)t);
+  sk = ((unsigned long long)__float_as_uint(key) << 32) | (2u * jl + (uint32_t)t);
   if (col) {
     if (V.color_mode == LR_COLOR_FLAT) {
       *col = __ldg(reinterpret_cast<const float4*>(V.col) + jl);
@@ -53,20 +63,16 @@ __device__ bool frag_eval(const Ws& ws, const ViewDev& V, uint32_t rec, int t, i
       uint4 q4;
       if (V.idx) q4 = __ldg(reinterpret_cast<const uint4*>(V.idx) + jl);
       else q4 = make_uint4(4 * jl, 4 * jl + 1, 4 * jl + 2, 4 * jl + 3);
-      const uint32_t vids[4] = {q4.x, q4.y, q4.z, q4.w};
-      const float l0 = __fmul_rn(__ll2float_rn(e[0]), inv);
-      const float ls[3] = {l0, l1, l2};
-      float4 num = make_float4(0.f, 0.f, 0.f, 0.f);
-      float den = 0.f;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float wk = ls[k] * R.q[vi[k]];
-        const float4 c = __ldg(reinterpret_cast<const float4*>(V.col) + vids[vi[k]]);
-        num.x += wk * c.x; num.y += wk * c.y; num.z += wk * c.z; num.w += wk * c.w;
-        den += wk;
-      }
-      const float r = 1.0f / den;
-      *col = make_float4(num.x * r, num.y * r, num.z * r, num.w * r);
+      const uint32_t va = q4.x;
+      const uint32_t vb = ib == 1 ? q4.y : (ib == 2 ? q4.z : q4.w);
+      const uint32_t vc = ic == 1 ? q4.y : (ic == 2 ? q4.z : q4.w);
+      const float wa = __fmul_rn(__ll2float_rn(e[0]), inv) * qa, wb = l1 * qb, wc = l2 * qc;
+      const float4 ca = __ldg(reinterpret_cast<const float4*>(V.col) + va);
+      const float4 cb = __ldg(reinterpret_cast<const float4*>(V.col) + vb);
+      const float4 cc = __ldg(reinterpret_cast<const float4*>(V.col) + vc);
+      const float r = 1.0f / (wa + wb + wc);
+      *col = make_float4((wa * ca.x + wb * cb.x + wc * cc.x) * r, (wa * ca.y + wb * cb.y + wc * cc.y) * r,
+                         (wa * ca.z + wb * cb.z + wc * cc.z) * r, (wa * ca.w + wb * cb.w + wc * cc.w) * r);
     }
   }
   return true;
@@ -110,7 +116,7 @@ __device__ void composite_sorted(const Ws& ws, const ViewDev& V, const unsigned 
     const uint32_t id = (uint32_t)sk;
     float4 col;
     unsigned long long dummy;
-    frag_eval(ws, V, (uint32_t)(V.quad_base + (id >> 1)), (int)(id & 1u), px, py, &dummy, &col);
+    frag_eval(ws, V, (uint32_t)(V.quad_base + (id >> 1)), (int)(id & 1u), px, py, dummy, &col);
     const float w = sT * col.w;
     sr += w * col.x; sg += w * col.y; sb += w * col.z;
     sT *= 1.0f - col.w;
@@ -195,7 +201,7 @@ __device__ void overflow_pixel(const Ws& ws, long long pid, unsigned long long* 
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
           unsigned long long sk = 0;
-          const bool cov = hit && frag_eval(ws, V, rec, t, px, py, &sk, nullptr) && sk < tau;
+          const bool cov = hit && frag_eval(ws, V, rec, t, px, py, sk, nullptr) && sk < tau;
           below += __popc(__ballot_sync(0xffffffffu, cov));
           const bool keep = cov && sk > lb;
           const unsigned m = __ballot_sync(0xffffffffu, keep);
