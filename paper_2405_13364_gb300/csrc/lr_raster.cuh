@@ -469,6 +469,7 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
       if (lane < nc) {
         const QuadRec R = load_rec(ws.rec, rec);
         const uint32_t jl = (uint32_t)(rec - V.quad_base);
+        uint32_t vsel = 0;   // per set-up triangle t: bit 8 + t, and its corners 1, 2 at bits 4t
 #pragma unroll 1
         for (int t = 0; t < 2; ++t) {
           TriSm& T = tris[2 * lane + t];
@@ -489,29 +490,39 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
             cor[0] = cg[0]; cor[1] = cg[1]; cor[2] = cg[2];
           }
           if (t == 0) tm0 = mk; else tm1 = mk;
-          if (VTX) {
-            float4* qc = qcs + (2 * lane + t) * 3;
-            if (!vtx_view) {
-              qc[0] = __ldg(reinterpret_cast<const float4*>(V.col) + jl);
-              T.eb.z |= (int)kTriFlatCol;
-            } else {
-              // corner colours times 1/w as (c0, c1 - c0, c2 - c0) for the fragment's
-              // c0 + l1 (c1 - c0) + l2 (c2 - c0)
-              uint4 vi = make_uint4(4 * jl, 4 * jl + 1, 4 * jl + 2, 4 * jl + 3);
-              if (V.idx) vi = __ldg(reinterpret_cast<const uint4*>(V.idx) + jl);
-              float4 a[3];
+          if (VTX) vsel |= (1u << (8 + t)) | ((uint32_t)(cor[1] | (cor[2] << 2)) << (4 * t));
+        }
+        if (VTX && vsel) {
+          if (!vtx_view) {
+            const float4 fc = __ldg(reinterpret_cast<const float4*>(V.col) + jl);
 #pragma unroll
-              for (int k = 0; k < 3; ++k) {
-                const int ck = cor[k];
-                const uint32_t vid = ck == 0 ? vi.x : (ck == 1 ? vi.y : (ck == 2 ? vi.z : vi.w));
-                const float qk = ck == 0 ? R.q[0] : (ck == 1 ? R.q[1] : (ck == 2 ? R.q[2] : R.q[3]));
-                const float4 cc = __ldg(reinterpret_cast<const float4*>(V.col) + vid);
-                a[k] = make_float4(qk * cc.x, qk * cc.y, qk * cc.z, qk * cc.w);
+            for (int t = 0; t < 2; ++t)
+              if (vsel & (1u << (8 + t))) {
+                qcs[(2 * lane + t) * 3] = fc;
+                tris[2 * lane + t].eb.z |= (int)kTriFlatCol;
               }
-              const float4 a0 = a[0], a1 = a[1], a2 = a[2];
-              qc[0] = a0;
-              qc[1] = make_float4(a1.x - a0.x, a1.y - a0.y, a1.z - a0.z, a1.w - a0.w);
-              qc[2] = make_float4(a2.x - a0.x, a2.y - a0.y, a2.z - a0.z, a2.w - a0.w);
+          } else {
+            // the quad's four corner colours times 1/w, loaded together once; each triangle
+            // stores (c0, c1 - c0, c2 - c0) of its corners for the fragment's
+            // c0 + l1 (c1 - c0) + l2 (c2 - c0)
+            uint4 vi = make_uint4(4 * jl, 4 * jl + 1, 4 * jl + 2, 4 * jl + 3);
+            if (V.idx) vi = __ldg(reinterpret_cast<const uint4*>(V.idx) + jl);
+            const float4* cv = reinterpret_cast<const float4*>(V.col);
+            const float4 c0 = __ldg(cv + vi.x), c1 = __ldg(cv + vi.y), c2 = __ldg(cv + vi.z), c3 = __ldg(cv + vi.w);
+            const float4 p0 = make_float4(R.q[0] * c0.x, R.q[0] * c0.y, R.q[0] * c0.z, R.q[0] * c0.w);
+            const float4 p1 = make_float4(R.q[1] * c1.x, R.q[1] * c1.y, R.q[1] * c1.z, R.q[1] * c1.w);
+            const float4 p2 = make_float4(R.q[2] * c2.x, R.q[2] * c2.y, R.q[2] * c2.z, R.q[2] * c2.w);
+            const float4 p3 = make_float4(R.q[3] * c3.x, R.q[3] * c3.y, R.q[3] * c3.z, R.q[3] * c3.w);
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+              if (!(vsel & (1u << (8 + t)))) continue;
+              const uint32_t kb = (vsel >> (4 * t)) & 3u, kc = (vsel >> (4 * t + 2)) & 3u;
+              const float4 a1 = kb == 1 ? p1 : (kb == 2 ? p2 : p3);
+              const float4 a2 = kc == 1 ? p1 : (kc == 2 ? p2 : p3);
+              float4* qc = qcs + (2 * lane + t) * 3;
+              qc[0] = p0;
+              qc[1] = make_float4(a1.x - p0.x, a1.y - p0.y, a1.z - p0.z, a1.w - p0.w);
+              qc[2] = make_float4(a2.x - p0.x, a2.y - p0.y, a2.z - p0.z, a2.w - p0.w);
             }
           }
         }
