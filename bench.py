@@ -45,8 +45,8 @@ LAUNCHES_PER_FRAME = 9
 RASTER_TRAFFIC = {
     # (DRAM read + write bytes per launch, ncu smsp__issue_active, ncu smsp__inst_executed,
     #  source hash of the captured build)
-    ("layers", 1, False): (102_275_072, 0.766, 464_419_215, "0fb5ca6b70d80b69"),      # profiles/k_raster_layers1080p.md
-    ("particles", 1, False): (388_662_272, 0.725, 1_066_088_790, "0fb5ca6b70d80b69"),  # profiles/k_raster_particles1080p.md
+    ("layers", 1, False): (102_847_488, 0.795, 458_509_652, "0651ad8b7a8e3445"),      # profiles/k_raster_layers1080p.md
+    ("particles", 1, False): (391_230_720, 0.724, 1_066_088_790, "0651ad8b7a8e3445"),  # profiles/k_raster_particles1080p.md
 }
 RASTER_SOURCES = ("lr_raster.cuh", "lr_common.cuh")
 LANES_PER_SM_CLK = 128
