@@ -468,15 +468,19 @@ __device__ bool cta_bucket_sort(unsigned long long* r, int n, unsigned long long
 // Ascending merge sort of g[0, n) (n <= kSortBigCap) in shared memory by the whole CTA:
 // 32-key runs sorted by warp shuffles, then merge levels between two shared buffers, each
 // thread producing an equal slice of every level's output (merge path search + a
-// sequential merge of its slice).
-__device__ void cta_merge_sort_smem(unsigned long long* g, int n, unsigned long long* A,
+// sequential merge of its slice). The keys are padded to a power of two N with the
+// largest key, so every output position from n on holds padding at every level: both
+// buffers are padded once, and the runs and output slices starting at n or later are
+// skipped.
+__device__ __forceinline__ void cta_merge_sort_smem(unsigned long long* g, int n, unsigned long long* A,
                                     unsigned long long* Bf) {
   int N = 32;
   while (N < n) N <<= 1;
   const int T = (int)blockDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = T >> 5;
   for (int i = t; i < N; i += T) A[i] = i < n ? g[i] : ~0ull;
+  for (int i = n + t; i < N; i += T) Bf[i] = ~0ull;
   __syncthreads();
-  for (int r = warp; r < N / 32; r += nw) {
+  for (int r = warp; 32 * r < n; r += nw) {
     unsigned long long v = A[32 * r + lane];
     for (int k = 2; k <= 32; k <<= 1)
       for (int j = k >> 1; j > 0; j >>= 1) {
@@ -491,7 +495,7 @@ __device__ void cta_merge_sort_smem(unsigned long long* g, int n, unsigned long 
   unsigned long long* dst = Bf;
   for (int w = 32; w < N; w <<= 1) {
     const int P = N / T > 0 ? N / T : 1;      // outputs per thread; divides 2w
-    for (int d0 = t * P; d0 < N; d0 += T * P) {
+    for (int d0 = t * P; d0 < n; d0 += T * P) {
       const int base = (d0 / (2 * w)) * (2 * w), loc = d0 - base;
       const unsigned long long* a = src + base;
       const unsigned long long* b = src + base + w;
@@ -529,7 +533,7 @@ __global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {
   write_hb_bitmap(ws, r, n, bin, reinterpret_cast<uint32_t*>(sbuf), (int)(kSortSmemBytes / 4));
 }
 
-__global__ __launch_bounds__(kSortBigThreads) void k_bin_sort_big(Ws ws) {
+__global__ __launch_bounds__(kSortBigThreads, 1) void k_bin_sort_big(Ws ws) {
   extern __shared__ unsigned long long sbuf[];
   __shared__ int s_bin;
   if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
