@@ -220,9 +220,9 @@ __device__ __forceinline__ uint32_t tri_mask_fast(const int e[3], const int sx[3
                                                   const int box[4]) {
   uint32_t mask = 0;
   const uint32_t cols = ((2u << box[1]) - 1u) & ~((1u << box[0]) - 1u);
-#pragma unroll 1
-  for (int ly = box[2]; ly <= box[3]; ++ly) {
-    uint32_t row = cols;
+#pragma unroll
+  for (int ly = 0; ly < kHbH; ++ly) {
+    uint32_t row = (ly >= box[2] && ly <= box[3]) ? cols : 0u;
 #pragma unroll
     for (int k = 0; k < 3; ++k)
       row &= row_cover((int)((uint32_t)e[k] + (uint32_t)ly * (uint32_t)sy[k]), sx[k]);
@@ -531,6 +531,7 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
       // ---- 3. transpose: lane = pixel, bit c = covered by triangle t of quad c -----------
       uint32_t m0 = warp_transpose32(tm0, lane), m1 = warp_transpose32(tm1, lane);
       if (!pix_ok) m0 = m1 = 0;
+      cnt += __popc(m0) + __popc(m1);
       // ---- 4. fragments in candidate order through the K-slot sorter -----------------
       // one fragment per iteration: the lowest candidate with a covering triangle, T0
       // before T1 when both cover the pixel
@@ -543,7 +544,6 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
           const TriSm& T = tris[2 * c + t];
           const int4 eb = T.eb;
           const uint32_t fl = (uint32_t)eb.z, id = (uint32_t)eb.w;
-          ++cnt;
           if (hashing) hsh += splitmix64(id);
           if (st.flagged) continue;
           const float4 kq = T.kq;
