@@ -470,7 +470,7 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
         const QuadRec R = load_rec(ws.rec, rec);
         const uint32_t jl = (uint32_t)(rec - V.quad_base);
         uint32_t vsel = 0;   // per set-up triangle t: bit 8 + t, and its corners 1, 2 at bits 4t
-#pragma unroll 1
+#pragma unroll
         for (int t = 0; t < 2; ++t) {
           TriSm& T = tris[2 * lane + t];
           int cor[3];
