@@ -336,8 +336,11 @@ __device__ void write_hb_bitmap(const Ws& ws, const unsigned long long* r, int n
       const int py0 = max((int)(rc.y & 0xffff), y0) - y0, py1 = min((int)(rc.y >> 16), y0 + kBin - 1) - y0;
       if (px0 <= px1 && py0 <= py1) {
         const int hx0 = px0 / kHbW, hx1 = px1 / kHbW, hy0 = py0 / kHbH, hy1 = py1 / kHbH;
+        // the half-block columns hx0..hx1 (4 bits) replicated into rows hy0..hy1 (a nibble
+        // per row): a product, since a row's nibble never carries into the next
         const uint32_t row = ((2u << hx1) - 1u) & ~((1u << hx0) - 1u);
-        for (int hy = hy0; hy <= hy1; ++hy) mask |= row << (hy * (kBin / kHbW));
+        const uint32_t rows = 0x11111111u & ((2u << (4 * hy1)) - 1u) & ~((1u << (4 * hy0)) - 1u);
+        mask = row * rows;
       }
     }
     dst[(size_t)lane * nw + w] = warp_transpose32(mask, lane);
