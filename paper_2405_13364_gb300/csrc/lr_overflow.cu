@@ -21,9 +21,8 @@ namespace lr {
 // Exact fragment of record rec, triangle t at pixel (px, py): returns false if the pixel
 // centre is not covered; otherwise the sort key and (if col) the straight RGBA colour.
 // The triangle's vertices are picked with selects, so the record stays in registers.
-__device__ __forceinline__ bool frag_eval(const Ws& ws, const ViewDev& V, uint32_t rec, int t, int px, int py,
-                                          unsigned long long& sk, float4* col) {
-  const QuadRec R = load_rec(ws.rec, rec);
+__device__ __forceinline__ bool frag_eval_r(const Ws& ws, const ViewDev& V, const QuadRec& R, uint32_t rec, int t,
+                                            int px, int py, unsigned long long& sk, float4* col) {
   if (!(R.info & (t ? kInfoTri1 : kInfoTri0))) return false;
   // triangle t = (v0, v[1 + t], v[2 + t]); a negative area swaps its last two vertices
   const bool sw = (R.info & (kInfoSwap0 << t)) != 0;
@@ -76,6 +75,12 @@ __device__ __forceinline__ bool frag_eval(const Ws& ws, const ViewDev& V, uint32
     }
   }
   return true;
+}
+
+__device__ __forceinline__ bool frag_eval(const Ws& ws, const ViewDev& V, uint32_t rec, int t, int px, int py,
+                                          unsigned long long& sk, float4* col) {
+  const QuadRec R = load_rec(ws.rec, rec);
+  return frag_eval_r(ws, V, R, rec, t, px, py, sk, col);
 }
 
 // descending bitonic sort of buf[0, n2) by one warp (n2 a power of two >= 32)
@@ -193,15 +198,27 @@ __device__ void overflow_pixel(const Ws& ws, long long pid, unsigned long long* 
     for (int g = 0; g < nw; g += 32) {
       BitRounds br;
       br.prepare(g + lane < nw ? __ldg(row + g + lane) : 0u, lane);
+      // candidates of the pixel's half-block, 32 per round; the next round's reference and
+      // quad record are loaded while the current round is evaluated
+      int jn = br.get(0, lane);
+      uint32_t recn = jn >= 0 ? ~(uint32_t)ws.refs[off + 32 * g + jn] : 0u;
+      QuadRec Rn = {};
+      if (jn >= 0) Rn = load_rec(ws.rec, recn);
       for (int r0 = 0; r0 < br.total; r0 += 32) {
-        const int j = br.get(r0, lane);
-        // candidates of the pixel's half-block; the exact test below decides coverage
+        const int j = jn;
+        const uint32_t rec = recn;
+        const QuadRec R = Rn;
+        if (r0 + 32 < br.total) {
+          jn = br.get(r0 + 32, lane);
+          recn = jn >= 0 ? ~(uint32_t)ws.refs[off + 32 * g + jn] : 0u;
+          if (jn >= 0) Rn = load_rec(ws.rec, recn);
+        }
+        // the exact test below decides coverage
         const bool hit = j >= 0;
-        const uint32_t rec = hit ? ~(uint32_t)ws.refs[off + 32 * g + j] : 0u;
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
           unsigned long long sk = 0;
-          const bool cov = hit && frag_eval(ws, V, rec, t, px, py, sk, nullptr) && sk < tau;
+          const bool cov = hit && frag_eval_r(ws, V, R, rec, t, px, py, sk, nullptr) && sk < tau;
           below += __popc(__ballot_sync(0xffffffffu, cov));
           const bool keep = cov && sk > lb;
           const unsigned m = __ballot_sync(0xffffffffu, keep);
