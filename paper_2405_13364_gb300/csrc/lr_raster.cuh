@@ -54,8 +54,8 @@ constexpr int kOvfThreads = 128;
 // shared-memory loads. Edges 1 (v2->v0) and 2 (v0->v1) give the barycentric numerators
 // of the depth key; edge 0 is only needed for coverage, which the masks already hold.
 struct __align__(16) TriSm {
-  int4 ea;         // e1, e2: biased edge values (E + owned - 1) at the half-block's first
-                   // pixel centre; sx1, sx2: change per pixel step in x
+  int4 ea;         // e1, e2: edge values E at the half-block's first pixel centre; sx1,
+                   // sx2: change per pixel step in x
   int4 eb;         // sy1, sy2: change per pixel step in y; flags; id (2 * quad + triangle)
   float4 kq;       // q0 = 1/w at v0, d1 = q1 - q0, d2 = q2 - q0, inv = 1 / (float)area
   int X[3], Y[3];  // vertices after the orientation fix (64-bit path)
@@ -134,7 +134,9 @@ static __device__ __noinline__ bool setup_tri(TriSm& T, const int X[4], const in
     if (!owned) flags |= 1u << (3 + k);
   }
   if (fast) flags |= kTriFast;
-  T.ea = make_int4(le[1], le[2], lsx[1], lsx[2]);
+  // the key's edge values unbiased (the masks use the biased ones in le)
+  T.ea = make_int4((int)((uint32_t)le[1] + ((flags >> 4) & 1u)), (int)((uint32_t)le[2] + ((flags >> 5) & 1u)), lsx[1],
+                   lsx[2]);
   T.eb = make_int4(lsy[1], lsy[2], (int)flags, (int)(2u * jl + (uint32_t)t));
   return true;
 }
@@ -179,7 +181,9 @@ __device__ __forceinline__ bool setup_tri_small(TriSm& T, const int X[4], const 
     lsy[k] = 256 * dx;
     if (!owned) flags |= 1u << (3 + k);
   }
-  T.ea = make_int4(le[1], le[2], lsx[1], lsx[2]);
+  // the key's edge values unbiased (the masks use the biased ones in le)
+  T.ea = make_int4((int)((uint32_t)le[1] + ((flags >> 4) & 1u)), (int)((uint32_t)le[2] + ((flags >> 5) & 1u)), lsx[1],
+                   lsx[2]);
   T.eb = make_int4(lsy[1], lsy[2], (int)flags, (int)(2u * jl + (uint32_t)t));
   return true;
 }
@@ -258,10 +262,8 @@ __device__ __forceinline__ float tri_key(const TriSm& T, int4 ea, int4 eb, float
   const uint32_t fl = (uint32_t)eb.z;
   float f1, f2;
   if (fl & kTriFast) {
-    const int e1 = (int)((uint32_t)ea.x + (uint32_t)lx * (uint32_t)ea.z + (uint32_t)ly * (uint32_t)eb.x +
-                         ((fl >> 4) & 1u));
-    const int e2 = (int)((uint32_t)ea.y + (uint32_t)lx * (uint32_t)ea.w + (uint32_t)ly * (uint32_t)eb.y +
-                         ((fl >> 5) & 1u));
+    const int e1 = (int)((uint32_t)ea.x + (uint32_t)lx * (uint32_t)ea.z + (uint32_t)ly * (uint32_t)eb.x);
+    const int e2 = (int)((uint32_t)ea.y + (uint32_t)lx * (uint32_t)ea.w + (uint32_t)ly * (uint32_t)eb.y);
     f1 = __int2float_rn(e1);
     f2 = __int2float_rn(e2);
   } else {
