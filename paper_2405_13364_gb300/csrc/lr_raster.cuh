@@ -7,7 +7,7 @@
 // bins first), so high-density bins are spread over many warps instead of one CTA.
 //
 // Per half-block (all from the bin's reference list, already sorted front to back by
-// k_bin_sort -- stage 1 of the two-stage sort):
+// k_bin_sort -- stage 1 of the two-stage sort, Sec. 2, Stage 3, Phase 2):
 //   1. candidates: the half-block's row of the bin's transposed bitmap (written by
 //      k_bin_sort: bit j set iff sorted reference j overlaps the half-block) is read with
 //      one coalesced load per 1024 references, and its set bits are handed out 32 at a
@@ -21,10 +21,12 @@
 //      pixels" into "pixel -> triangles", one bit per covering triangle in each lane;
 //   4. fragments, per lane in candidate order: the exact depth key of the fragment
 //      (interpolated 1/w, identical bit for bit to the oracle's formula) is pushed into a
-//      K-slot register sorter (stage 2, the paper's "depth filter"). When full,
+//      K-slot register sorter (stage 2, the paper's depth filter, Sec. 2, Stage 3,
+//      Phase 3, "Sample blending"). When full,
 //      the nearest element is evicted and blended front to back. If a fragment arrives
 //      that is nearer than the last evicted one, the stream was not in order for this
-//      pixel: the pixel is flagged and registered for k_overflow.
+//      pixel: the pixel is flagged (the paper's misorder detection, same passage) and
+//      registered for k_overflow.
 // Sort keys are (float bits of key) << 32 | (2 * quad + triangle): distinct per pixel, so
 // the per-pixel order is total and the result is unique.
 #pragma once
