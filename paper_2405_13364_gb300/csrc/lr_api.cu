@@ -47,6 +47,7 @@ LR_DECLARE_RASTER(8)
 LR_DECLARE_RASTER(12)
 
 __global__ void k_write_views(ViewChunk chunk, ViewDev* dst) {
+  pdl_begin();
   const int i = threadIdx.x;
   if (i < chunk.count) dst[chunk.first + i] = chunk.v[i];
 }
@@ -471,21 +472,21 @@ static lr_status launch_sequence(lr_ctx* ctx, const Prepared& P, cudaStream_t st
       more.first = first;
       more.count = std::min(kViewsPerLaunch, n_views - first);
       for (int i = 0; i < more.count; ++i) more.v[i] = P.vd[first + i];
-      k_write_views<<<1, 32, 0, st>>>(more, P.views_dev);
+      launch_pdl(k_write_views, dim3(1), dim3(32), 0, st, more, P.views_dev);
     }
   }
-  k_init<<<std::max(1, (L.total_bins + 255) / 256), 256, 0, st>>>(ws, (unsigned long long)L.refs_cap, chunk,
-                                                                  P.views_dev);
-  if (L.total_quads > 0) k_setup<<<(unsigned)((L.total_quads + 255) / 256), 256, 0, st>>>(ws);
+  launch_pdl(k_init, dim3(std::max(1, (L.total_bins + 255) / 256)), dim3(256), 0, st, ws,
+             (unsigned long long)L.refs_cap, chunk, P.views_dev);
+  if (L.total_quads > 0) launch_pdl(k_setup, dim3((unsigned)((L.total_quads + 255) / 256)), dim3(256), 0, st, ws);
   rec(ctx, timed, 1, st);
-  if (L.total_chunks > 0) k_bin_count<<<L.total_chunks, kBinThreads, 0, st>>>(ws);
+  if (L.total_chunks > 0) launch_pdl(k_bin_count, dim3(L.total_chunks), dim3(kBinThreads), 0, st, ws);
   rec(ctx, timed, 2, st);
-  k_bin_scan<<<1, 1024, 0, st>>>(ws);
+  launch_pdl(k_bin_scan, dim3(1), dim3(1024), 0, st, ws);
   rec(ctx, timed, 3, st);
-  if (L.total_chunks > 0) k_bin_scatter<<<L.total_chunks, kBinThreads, 0, st>>>(ws);
+  if (L.total_chunks > 0) launch_pdl(k_bin_scatter, dim3(L.total_chunks), dim3(kBinThreads), 0, st, ws);
   rec(ctx, timed, 4, st);
-  k_bin_sort<<<L.total_bins, 256, kSortSmemBytes, st>>>(ws);
-  k_bin_sort_big<<<ctx->sms, kSortBigThreads, kSortBigSmemBytes, st>>>(ws);
+  launch_pdl(k_bin_sort, dim3(L.total_bins), dim3(256), kSortSmemBytes, st, ws);
+  launch_pdl(k_bin_sort_big, dim3(ctx->sms), dim3(kSortBigThreads), kSortBigSmemBytes, st, ws);
   rec(ctx, timed, 5, st);
   const bool carry = P.any_vertex || (ctx->cfg.flags & LR_FLAG_CARRY_COLORS);
   const int mode = bwd ? 2 : ((carry ? 1 : 0) | (P.any_hash ? 4 : 0));

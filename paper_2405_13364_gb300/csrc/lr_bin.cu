@@ -128,6 +128,7 @@ __device__ __forceinline__ void for_each_ref(const Ws& ws, const ViewDev& V, lon
 // count and scatter are latency-bound (gathers, atomics): 5 resident CTAs per SM (48
 // registers, a few spills) measured faster than the 3 that 64-74 registers allow
 __global__ __launch_bounds__(kBinThreads, 5) void k_bin_count(Ws ws) {
+  pdl_begin();
   __shared__ uint32_t hist[kHistSmemBins];
   const int v = view_of_chunk(ws.views, ws.n_views, blockIdx.x);
   const ViewDev& V = ws.views[v];
@@ -173,6 +174,7 @@ __global__ __launch_bounds__(kBinThreads, 5) void k_bin_count(Ws ws) {
 // Single CTA. Offsets (exclusive scan), capacity check, and the bin order for the
 // rasteriser: bins by decreasing size class (floor(log2(count)) + 1), empty bins last.
 __global__ __launch_bounds__(1024) void k_bin_scan(Ws ws) {
+  pdl_begin();
   __shared__ unsigned long long warp_sums[32];
   __shared__ uint32_t cls_count[34];
   __shared__ uint32_t cls_base[34];
@@ -253,6 +255,7 @@ __global__ __launch_bounds__(1024) void k_bin_scan(Ws ws) {
 }
 
 __global__ __launch_bounds__(kBinThreads, 5) void k_bin_scatter(Ws ws) {
+  pdl_begin();
   __shared__ uint32_t hist[kHistSmemBins];
   if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
   const int v = view_of_chunk(ws.views, ws.n_views, blockIdx.x);
@@ -524,6 +527,7 @@ __device__ __forceinline__ void cta_merge_sort_smem(unsigned long long* g, int n
 }
 
 __global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {
+  pdl_begin();
   extern __shared__ unsigned long long sbuf[];
   if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
   const int bin = blockIdx.x;
@@ -539,6 +543,7 @@ __global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {
 }
 
 __global__ __launch_bounds__(kSortBigThreads, 1) void k_bin_sort_big(Ws ws) {
+  pdl_begin();
   extern __shared__ unsigned long long sbuf[];
   __shared__ int s_bin;
   if (ws.ctrl->error == LR_ERR_OVERFLOW) return;

@@ -11,6 +11,8 @@
 
 #include "lr.h"
 
+#include <utility>
+
 namespace lr {
 
 constexpr int kBinLog2 = 5;                 // 32x32-pixel bins (Sec. 2, Stage 2)
@@ -83,6 +85,33 @@ struct ViewChunk {
   ViewDev v[kViewsPerLaunch];
   int first, count;
 };
+
+// Programmatic dependent launch (sm_90 and later). The pipeline's kernels (all but the
+// rasteriser) are launched with programmatic stream serialisation (launch_pdl), so each
+// may be scheduled while its predecessor in the stream drains; every kernel first waits
+// for its predecessor's completion and memory (griddepcontrol.wait: nothing of the kernel
+// touches memory before it), then lets its own successor begin launching. A kernel
+// launched without the attribute passes both instructions at once.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+static inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                     Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Device control block at the start of the workspace.
 struct Ctrl {

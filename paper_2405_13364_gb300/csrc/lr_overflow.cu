@@ -253,6 +253,7 @@ __device__ void overflow_pixel(const Ws& ws, long long pid, unsigned long long* 
 // the exact path over the registered pixel list
 template <bool BWD>
 __global__ __launch_bounds__(kOvfThreads) void k_overflow(Ws ws) {
+  pdl_begin();
   __shared__ unsigned long long sbuf[kOvfThreads / 32][kOvfBuf];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
@@ -271,9 +272,8 @@ cudaError_t overflow_occupancy(int* blocks_per_sm) {
 }
 
 cudaError_t launch_overflow(bool bwd, const Ws& ws, int grid, cudaStream_t st) {
-  if (bwd) k_overflow<true><<<grid, kOvfThreads, 0, st>>>(ws);
-  else k_overflow<false><<<grid, kOvfThreads, 0, st>>>(ws);
-  return cudaGetLastError();
+  if (bwd) return launch_pdl(k_overflow<true>, dim3(grid), dim3(kOvfThreads), 0, st, ws);
+  return launch_pdl(k_overflow<false>, dim3(grid), dim3(kOvfThreads), 0, st, ws);
 }
 
 }  // namespace lr

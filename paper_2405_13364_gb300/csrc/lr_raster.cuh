@@ -423,6 +423,7 @@ __device__ __forceinline__ void write_pixel(const ViewDev& V, long long pidx, fl
 // others carry no code or registers for it.
 template <int K, bool VTX, bool BWD, bool HASH>
 __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster(Ws ws) {
+  pdl_begin();
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lx = lane & (kHbW - 1), ly = lane >> 3;
@@ -684,6 +685,8 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
   /* mode: 0 flat colours, 1 colours in the sorter, 2 backward; + 4: coverage hash */        \
   cudaError_t launch_raster_##KK(int mode, const Ws& ws, int grid, cudaStream_t st) {         \
     const size_t sf = raster_smem_bytes(false), sv = raster_smem_bytes(true);                 \
+    /* a plain launch: with programmatic serialisation the persistent CTAs, placed early  \
+       next to the bin sort's, measured slower on the particle frame */                       \
     switch (mode) {                                                                           \
       case 1: k_raster<KK, true, false, false><<<grid, kRasterThreads, sv, st>>>(ws); break;  \
       case 2: k_raster<KK, false, true, false><<<grid, kRasterThreads, raster_smem_bytes(false, true), st>>>(ws); break; \

@@ -27,6 +27,7 @@ namespace lr {
 // Launched with block 0 covering the whole control block, so the final store of refs_cap is
 // ordered after its zeroing.
 __global__ void k_init(Ws ws, unsigned long long refs_cap, ViewChunk views, ViewDev* views_dst) {
+  pdl_begin();
   if (blockIdx.x == 0 && threadIdx.x < views.count) views_dst[views.first + threadIdx.x] = views.v[threadIdx.x];
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -42,6 +43,7 @@ __device__ __forceinline__ float row_dot(const float* m, float x, float y, float
 }
 
 __global__ __launch_bounds__(256) void k_setup(Ws ws) {
+  pdl_begin();
   const long long g = blockIdx.x * 256LL + threadIdx.x;
   const bool active = g < ws.total_quads;
   uint32_t reason = kVisible;
