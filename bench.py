@@ -45,8 +45,8 @@ LAUNCHES_PER_FRAME = 9
 RASTER_TRAFFIC = {
     # (DRAM read + write bytes per launch, ncu smsp__issue_active, ncu smsp__inst_executed,
     #  source hash of the captured build)
-    ("layers", 1, False): (101_920_256, 0.786, 392_615_520, "378b6e2e0cd73189"),      # profiles/k_raster_layers1080p.md
-    ("particles", 1, False): (380_882_944, 0.710, 906_686_705, "378b6e2e0cd73189"),  # profiles/k_raster_particles1080p.md
+    ("layers", 1, False): (102_125_056, 0.786, 392_622_816, "a5f3cc2466cfb7ff"),      # profiles/k_raster_layers1080p.md
+    ("particles", 1, False): (382_462_976, 0.709, 906_694_001, "a5f3cc2466cfb7ff"),  # profiles/k_raster_particles1080p.md
 }
 RASTER_SOURCES = ("lr_raster.cuh", "lr_common.cuh")
 LANES_PER_SM_CLK = 128

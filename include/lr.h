@@ -55,9 +55,15 @@ enum { LR_COLOR_FLAT = 0, LR_COLOR_VERTEX = 1 };
 /* lr_config.flags */
 enum {
   LR_FLAG_TIMING = 1,       /* record per-stage CUDA events; lr_get_stats reports stage_ms */
-  LR_FLAG_CARRY_COLORS = 2  /* flat-colour scenes too: the per-pixel sorter carries each
+  LR_FLAG_CARRY_COLORS = 2, /* flat-colour scenes too: the per-pixel sorter carries each
                                fragment's colour (fetched once per half-block) instead of
                                reading it when the fragment is blended (a tuning choice) */
+  LR_FLAG_NO_PDL = 4        /* launch without programmatic dependent launch. By default each
+                               kernel of a render may be scheduled while its predecessor
+                               drains (it waits for it before touching memory); a context
+                               rendering on several streams at once sets this flag, since
+                               such waiting kernels hold SM resources other streams need.
+                               The server's own context always sets it. */
 };
 
 /* Creation-time parameters. Zero selects the default. */

@@ -31,6 +31,7 @@ LR_COLOR_FLAT = 0
 LR_COLOR_VERTEX = 1
 LR_FLAG_TIMING = 1
 LR_FLAG_CARRY_COLORS = 2
+LR_FLAG_NO_PDL = 4
 
 
 class LrError(RuntimeError):

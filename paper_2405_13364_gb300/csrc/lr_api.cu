@@ -33,7 +33,7 @@ __global__ void k_bin_scatter(Ws ws);
 __global__ void k_bin_sort(Ws ws);
 __global__ void k_bin_sort_big(Ws ws);
 cudaError_t overflow_occupancy(int* blocks_per_sm);
-cudaError_t launch_overflow(bool bwd, const Ws& ws, int grid, cudaStream_t st);
+cudaError_t launch_overflow(bool bwd, const Ws& ws, int grid, cudaStream_t st, bool pdl);
 
 #define LR_DECLARE_RASTER(KK)                                                       \
   cudaError_t prepare_raster_##KK(int* blocks_flat, int* blocks_vtx, int* blocks_bwd); \
@@ -456,6 +456,7 @@ static lr_status launch_sequence(lr_ctx* ctx, const Prepared& P, cudaStream_t st
     ws.bwd_mask = bwd->exact_mask;
   }
   const int n_views = ws.n_views;
+  const bool pdl = (ctx->cfg.flags & LR_FLAG_NO_PDL) == 0;
   rec(ctx, timed, 0, st);
   // the first kViewsPerLaunch descriptors travel with k_init, further ones with k_write_views
   ViewChunk chunk;
@@ -472,21 +473,21 @@ static lr_status launch_sequence(lr_ctx* ctx, const Prepared& P, cudaStream_t st
       more.first = first;
       more.count = std::min(kViewsPerLaunch, n_views - first);
       for (int i = 0; i < more.count; ++i) more.v[i] = P.vd[first + i];
-      launch_pdl(k_write_views, dim3(1), dim3(32), 0, st, more, P.views_dev);
+      launch_pdl(pdl, k_write_views, dim3(1), dim3(32), 0, st, more, P.views_dev);
     }
   }
-  launch_pdl(k_init, dim3(std::max(1, (L.total_bins + 255) / 256)), dim3(256), 0, st, ws,
+  launch_pdl(pdl, k_init, dim3(std::max(1, (L.total_bins + 255) / 256)), dim3(256), 0, st, ws,
              (unsigned long long)L.refs_cap, chunk, P.views_dev);
-  if (L.total_quads > 0) launch_pdl(k_setup, dim3((unsigned)((L.total_quads + 255) / 256)), dim3(256), 0, st, ws);
+  if (L.total_quads > 0) launch_pdl(pdl, k_setup, dim3((unsigned)((L.total_quads + 255) / 256)), dim3(256), 0, st, ws);
   rec(ctx, timed, 1, st);
-  if (L.total_chunks > 0) launch_pdl(k_bin_count, dim3(L.total_chunks), dim3(kBinThreads), 0, st, ws);
+  if (L.total_chunks > 0) launch_pdl(pdl, k_bin_count, dim3(L.total_chunks), dim3(kBinThreads), 0, st, ws);
   rec(ctx, timed, 2, st);
-  launch_pdl(k_bin_scan, dim3(1), dim3(1024), 0, st, ws);
+  launch_pdl(pdl, k_bin_scan, dim3(1), dim3(1024), 0, st, ws);
   rec(ctx, timed, 3, st);
-  if (L.total_chunks > 0) launch_pdl(k_bin_scatter, dim3(L.total_chunks), dim3(kBinThreads), 0, st, ws);
+  if (L.total_chunks > 0) launch_pdl(pdl, k_bin_scatter, dim3(L.total_chunks), dim3(kBinThreads), 0, st, ws);
   rec(ctx, timed, 4, st);
-  launch_pdl(k_bin_sort, dim3(L.total_bins), dim3(256), kSortSmemBytes, st, ws);
-  launch_pdl(k_bin_sort_big, dim3(ctx->sms), dim3(kSortBigThreads), kSortBigSmemBytes, st, ws);
+  launch_pdl(pdl, k_bin_sort, dim3(L.total_bins), dim3(256), kSortSmemBytes, st, ws);
+  launch_pdl(pdl, k_bin_sort_big, dim3(ctx->sms), dim3(kSortBigThreads), kSortBigSmemBytes, st, ws);
   rec(ctx, timed, 5, st);
   const bool carry = P.any_vertex || (ctx->cfg.flags & LR_FLAG_CARRY_COLORS);
   const int mode = bwd ? 2 : ((carry ? 1 : 0) | (P.any_hash ? 4 : 0));
@@ -494,7 +495,7 @@ static lr_status launch_sequence(lr_ctx* ctx, const Prepared& P, cudaStream_t st
   cudaError_t e = ctx->variant->launch(mode, ws, ctx->sms * rblocks, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "raster launch");
   rec(ctx, timed, 6, st);
-  e = launch_overflow(bwd != nullptr, ws, ctx->sms * ctx->ovf_blocks, st);
+  e = launch_overflow(bwd != nullptr, ws, ctx->sms * ctx->ovf_blocks, st, pdl);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "overflow launch");
   rec(ctx, timed, 7, st);
   e = cudaGetLastError();

@@ -38,7 +38,7 @@ __global__ void k_bin_sort_big(Ws ws);
 cudaError_t prepare_raster_3(int* blocks_flat, int* blocks_vtx, int* blocks_bwd);
 cudaError_t launch_raster_3(int mode, const Ws& ws, int grid, cudaStream_t st);
 cudaError_t overflow_occupancy(int* blocks_per_sm);
-cudaError_t launch_overflow(bool bwd, const Ws& ws, int grid, cudaStream_t st);
+cudaError_t launch_overflow(bool bwd, const Ws& ws, int grid, cudaStream_t st, bool pdl);
 }  // namespace lr
 
 using namespace lr;
@@ -207,7 +207,7 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
   const bool vtx_kernel = Q > 0 && vtx;
   if (launch_raster_3(vtx_kernel ? 1 : 0, ws, ds.sms * (vtx_kernel ? ds.blocks_vtx : ds.blocks_flat), st) != cudaSuccess)
     return LR_ERR_CUDA;
-  if (launch_overflow(false, ws, ds.sms * ds.ovf_blocks, st) != cudaSuccess) return LR_ERR_CUDA;
+  if (launch_overflow(false, ws, ds.sms * ds.ovf_blocks, st, false) != cudaSuccess) return LR_ERR_CUDA;
   if (device_status) k_noalloc_status<<<1, 1, 0, st>>>(ws.ctrl, device_status);
   return cudaGetLastError() == cudaSuccess ? LR_OK : LR_ERR_CUDA;
 }

@@ -271,9 +271,9 @@ cudaError_t overflow_occupancy(int* blocks_per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_overflow<false>, kOvfThreads, 0);
 }
 
-cudaError_t launch_overflow(bool bwd, const Ws& ws, int grid, cudaStream_t st) {
-  if (bwd) return launch_pdl(k_overflow<true>, dim3(grid), dim3(kOvfThreads), 0, st, ws);
-  return launch_pdl(k_overflow<false>, dim3(grid), dim3(kOvfThreads), 0, st, ws);
+cudaError_t launch_overflow(bool bwd, const Ws& ws, int grid, cudaStream_t st, bool pdl) {
+  if (bwd) return launch_pdl(pdl, k_overflow<true>, dim3(grid), dim3(kOvfThreads), 0, st, ws);
+  return launch_pdl(pdl, k_overflow<false>, dim3(grid), dim3(kOvfThreads), 0, st, ws);
 }
 
 }  // namespace lr

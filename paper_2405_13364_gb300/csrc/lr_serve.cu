@@ -191,6 +191,7 @@ extern "C" lr_status lr_server_start(lr_ctx* ctx, const lr_server_config* config
   memset(&s->stats, 0, sizeof(s->stats));
   lr_config inner_cfg = *lr_internal_config(ctx);
   inner_cfg.flags &= ~LR_FLAG_TIMING;
+  inner_cfg.flags |= LR_FLAG_NO_PDL;   // batches render on several streams at once
   lr_status st = lr_create(&inner_cfg, &s->inner);
   if (st != LR_OK) {
     delete s;
