@@ -11,6 +11,8 @@ Functions (each follows the definition stated in ``lr_oracle.c``):
   render(scene)                fp32 image, per-pixel fragment count and coverage hash,
                                8-bit image, the fp64 composite of the same fragment order
   render_pixels(scene, xs, ys) the same quantities for selected pixels only
+  render_threshold(scene, t)   the opt-in lossy alpha-threshold composite (front to back,
+                               a fragment blended only while transmittance > t)
   render64(scene, colors64)    fp64 forward (flat colours) used for finite differences
   backward(scene, grad_out)    fp64 gradient w.r.t. flat per-quad RGBA (Sec. 2 blending,
                                differentiated)
@@ -69,6 +71,8 @@ def _bind(lib):
     lib.or_render.argtypes = [ctypes.POINTER(_Scene), ctypes.c_int, P, P, P, P, P,
                               ctypes.POINTER(_Stats)]
     lib.or_render64.argtypes = [ctypes.POINTER(_Scene), ctypes.c_int, P, P]
+    lib.or_render_threshold.argtypes = [ctypes.POINTER(_Scene), ctypes.c_int, ctypes.c_float,
+                                        P, P, P, P]
     lib.or_backward.argtypes = [ctypes.POINTER(_Scene), ctypes.c_int, P, P, P]
     lib.or_render_pixels.argtypes = [ctypes.POINTER(_Scene), ctypes.c_int, ctypes.c_int64,
                                      P, P, P, P, P]
@@ -76,7 +80,7 @@ def _bind(lib):
     lib.or_pixel_fragments.argtypes = [ctypes.POINTER(_Scene), ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int64, P, P, P, P]
     lib.or_pixel_fragments.restype = ctypes.c_int64
-    for f in (lib.or_setup, lib.or_render, lib.or_render64, lib.or_backward,
+    for f in (lib.or_setup, lib.or_render, lib.or_render64, lib.or_render_threshold, lib.or_backward,
               lib.or_render_pixels, lib.or_num_threads):
         f.restype = ctypes.c_int
     return lib
@@ -200,6 +204,23 @@ def pixel_fragments(scene, px: int, py: int, cap: int = 4096):
                                _ptr(rgba))
     n = min(n, cap)
     return dict(key=key[:n], quad=quad[:n], tri=tri[:n], rgba=rgba[:n])
+
+
+def render_threshold(scene, t_min: float = 1.0 / 128.0, nthreads: int = 0):
+    """Alpha-threshold composite: rgba, per-pixel fragments blended (nblend), fragment
+    count, and the relative distance of T to t_min at the stop tests (margin)."""
+    lib = _load()
+    b = _Bound(scene)
+    H, W = scene.height, scene.width
+    rgba = np.zeros((H, W, 4), np.float32)
+    nblend = np.zeros((H, W), np.uint32)
+    count = np.zeros((H, W), np.uint32)
+    margin = np.zeros((H, W), np.float32)
+    rc = lib.or_render_threshold(ctypes.byref(b.s), nthreads, float(t_min), _ptr(rgba),
+                                 _ptr(nblend), _ptr(count), _ptr(margin))
+    if rc != 0:
+        raise RuntimeError(f"oracle render_threshold failed ({rc})")
+    return dict(rgba=rgba, nblend=nblend, count=count, margin=margin)
 
 
 def render64(scene, colors64=None, nthreads: int = 0):

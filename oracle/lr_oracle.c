@@ -36,6 +36,12 @@
  *   O.11 composite  C = a c + (1-a) C, A = a + (1-a) A, from black transparent.
  *   O.12 8-bit      rint(clamp(v,0,1) * 255).
  *   O.13 backward   fp64 gradient of the composite w.r.t. flat per-quad RGBA.
+ *   alpha threshold (opt-in, lossy; Sec. 2 "Sample blending", Sec. 3 "Alpha threshold"):
+ *                   composite front to back (the paper's order), blending a fragment
+ *                   only while the transmittance T = prod(1 - a) of the fragments in
+ *                   front of it is above t_min (the paper stops at accumulated alpha
+ *                   1 - 1/128, i.e. t_min = 1/128); T is the running fp32 product, one
+ *                   rounding per operation, so the stop decision is taken in fp32.
  */
 #include <math.h>
 #include <pthread.h>
@@ -299,7 +305,12 @@ typedef struct {
   const double* colors64;     /* flat [Q][4] used by the fp64 forward, NULL = s->colors */
   const double* grad_out;     /* [H][W][4] */
   double* grad_colors;        /* per-thread [nthreads][Q][4] */
-  int mode;                   /* 0 forward fp32, 1 fp64 forward, 2 backward */
+  int mode;                   /* 0 forward fp32, 1 fp64 forward, 2 backward,
+                                 3 alpha-threshold forward */
+  /* alpha threshold */
+  float t_min;                /* blend while T > t_min */
+  uint32_t* nblend;           /* [H][W] fragments blended before the stop */
+  float* margin;              /* [H][W] min |T - t_min| / t_min over the stop tests made */
   /* work distribution */
   pthread_mutex_t lock;
   int next_band;
@@ -347,6 +358,32 @@ static void composite_pixel(or_job* job, const or_frag* f, int64_t n, int64_t pi
     }
     if (job->count) job->count[pixel_index] = (uint32_t)n;
     if (job->hash) job->hash[pixel_index] = h;
+    return;
+  }
+  if (job->mode == 3) {
+    /* alpha threshold: f[] is ascending (back first), so walk it from the end */
+    float C[3] = {0.f, 0.f, 0.f}, T = 1.0f, margin = INFINITY;
+    uint32_t nb = 0;
+    for (int64_t i = n - 1; i >= 0; --i) {
+      if (job->t_min > 0.0f) {
+        float d = fabsf(T - job->t_min) / job->t_min;
+        if (d < margin) margin = d;
+      }
+      if (!(T > job->t_min)) break;   /* accumulated alpha 1 - T reached 1 - t_min */
+      float a = f[i].rgba[3];
+      float w = T * a;
+      for (int c = 0; c < 3; ++c) {
+        float wc = w * f[i].rgba[c];
+        C[c] = C[c] + wc;
+      }
+      T = T * (1.0f - a);
+      nb++;
+    }
+    float out[4] = {C[0], C[1], C[2], 1.0f - T};
+    for (int c = 0; c < 4; ++c) job->rgba[pixel_index * 4 + c] = out[c];
+    if (job->nblend) job->nblend[pixel_index] = nb;
+    if (job->margin) job->margin[pixel_index] = margin;
+    if (job->count) job->count[pixel_index] = (uint32_t)n;
     return;
   }
   /* fp64 colours for the fp64 forward and the backward */
@@ -544,6 +581,20 @@ int or_render(const or_scene* s, int nthreads, float* rgba, uint32_t* count, uin
   job.s = s; job.rgba = rgba; job.count = count; job.hash = hash; job.rgba8 = rgba8;
   job.rgba64 = rgba64; job.mode = 0;
   return run_job(&job, nthreads, st);
+}
+
+/* Alpha-threshold composite (see the header): rgba [H][W][4], per-pixel number of
+ * fragments blended, per-pixel fragment count, and how close T came to t_min at the stop
+ * tests (relative; a pixel with a small margin may stop one fragment earlier or later
+ * under another rounding of its alphas). */
+int or_render_threshold(const or_scene* s, int nthreads, float t_min, float* rgba, uint32_t* nblend,
+                        uint32_t* count, float* margin) {
+  if (!(t_min >= 0.0f && t_min < 1.0f)) return -2;
+  or_job job;
+  memset(&job, 0, sizeof(job));
+  job.s = s; job.rgba = rgba; job.count = count; job.mode = 3;
+  job.t_min = t_min; job.nblend = nblend; job.margin = margin;
+  return run_job(&job, nthreads, NULL);
 }
 
 int or_render64(const or_scene* s, int nthreads, const double* colors64, double* rgba64) {

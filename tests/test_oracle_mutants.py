@@ -5,6 +5,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_pins as pins
+from tests import test_oracle_threshold as tpins
 
 MUTANTS = {
     # fill rule: right/bottom edges owned instead of left/top
@@ -40,6 +41,12 @@ MUTANTS = {
     # composite forgets to attenuate what is behind
     "over_no_attenuation": ("float keep = om * C[c];", "float keep = C[c];",
                             [pins.test_two_layers_closed_form_and_order]),
+    # alpha threshold: the stop test made strict (T = t_min keeps blending)
+    "threshold_strict": ("if (!(T > job->t_min)) break;", "if (!(T >= job->t_min)) break;",
+                         [tpins.test_stack_closed_form]),
+    # alpha threshold: fragments weighted by their own alpha only (no transmittance)
+    "threshold_no_transmittance": ("float w = T * a;", "float w = a;",
+                                   [tpins.test_stack_closed_form]),
     # near plane ignored
     "no_near_cull": ("} else if (!(w >= s->near_z && w <= s->far_z)) {",
                      "} else if (!(w <= s->far_z)) {",
@@ -51,6 +58,8 @@ def _call(test):
     # parametrised pins: run the default-argument form of each
     if test is pins.test_rect_coverage_closed_form:
         test(False, 0)
+    elif test is tpins.test_stack_closed_form:
+        test(0.5, 7)
     else:
         test()
 
