@@ -58,12 +58,23 @@ enum {
   LR_FLAG_CARRY_COLORS = 2, /* flat-colour scenes too: the per-pixel sorter carries each
                                fragment's colour (fetched once per half-block) instead of
                                reading it when the fragment is blended (a tuning choice) */
-  LR_FLAG_NO_PDL = 4        /* launch without programmatic dependent launch. By default each
+  LR_FLAG_NO_PDL = 4,       /* launch without programmatic dependent launch. By default each
                                kernel of a render may be scheduled while its predecessor
                                drains (it waits for it before touching memory); a context
                                rendering on several streams at once sets this flag, since
                                such waiting kernels hold SM resources other streams need.
                                The server's own context always sets it. */
+  LR_FLAG_ALPHA_THRESHOLD = 8 /* opt-in, lossy (Sec. 2 "Sample blending", Sec. 3 "Alpha
+                               threshold"): a pixel stops blending once its accumulated alpha
+                               reaches 1 - 1/128, i.e. each fragment is blended only while the
+                               fp32 transmittance T = prod (1 - a) of the fragments in front of
+                               it (in exact depth order) is above 1/128. The image then differs
+                               from the exact composite by at most 1/128 per channel. Candidate
+                               quads that cannot reach in front of any unfinished pixel of a
+                               half-block are skipped, so lr_stats.fragments counts the
+                               fragments evaluated. Renders that ask for frag_count or cov_hash
+                               and lr_render_backward return LR_ERR_UNSUPPORTED on such a
+                               context. */
 };
 
 /* Creation-time parameters. Zero selects the default. */

@@ -32,6 +32,7 @@ LR_COLOR_VERTEX = 1
 LR_FLAG_TIMING = 1
 LR_FLAG_CARRY_COLORS = 2
 LR_FLAG_NO_PDL = 4
+LR_FLAG_ALPHA_THRESHOLD = 8
 
 
 class LrError(RuntimeError):

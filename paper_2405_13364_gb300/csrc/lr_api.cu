@@ -432,6 +432,8 @@ static lr_status prepare(lr_ctx* ctx, int32_t n_views, const lr_view* views, voi
   for (int i = 0; i < n_views; ++i) {
     lr_status s = check_view(ctx, views[i]);
     if (s != LR_OK) return s;
+    if ((ctx->cfg.flags & LR_FLAG_ALPHA_THRESHOLD) && (views[i].target.frag_count || views[i].target.cov_hash))
+      return fail(ctx, LR_ERR_UNSUPPORTED, "fragment counts and coverage hashes need the exact composite%s");
   }
   lr_status s = layout_for(ctx, n_views, views, &P->L);
   if (s != LR_OK) return s;
@@ -490,7 +492,9 @@ static lr_status launch_sequence(lr_ctx* ctx, const Prepared& P, cudaStream_t st
   launch_pdl(pdl, k_bin_sort_big, dim3(ctx->sms), dim3(kSortBigThreads), kSortBigSmemBytes, st, ws);
   rec(ctx, timed, 5, st);
   const bool carry = P.any_vertex || (ctx->cfg.flags & LR_FLAG_CARRY_COLORS);
-  const int mode = bwd ? 2 : ((carry ? 1 : 0) | (P.any_hash ? 4 : 0));
+  const bool ath = !bwd && (ctx->cfg.flags & LR_FLAG_ALPHA_THRESHOLD);   // no hash then (prepare)
+  const int mode = bwd ? 2 : ((carry ? 1 : 0) | (P.any_hash ? 4 : 0) | (ath ? 8 : 0));
+  ws.t_min = ath ? kAlphaTMin : 0.0f;
   const int rblocks = bwd ? ctx->raster_blocks_bwd : (carry ? ctx->raster_blocks_vtx : ctx->raster_blocks_flat);
   cudaError_t e = ctx->variant->launch(mode, ws, ctx->sms * rblocks, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "raster launch");
@@ -649,6 +653,8 @@ extern "C" lr_status lr_render_backward(lr_ctx* ctx, const lr_quads* quads, cons
     return fail(ctx, LR_ERR_INVALID_ARG, "null argument%s");
   if (quads->num_quads > 0 && quads->color_mode != LR_COLOR_FLAT)
     return fail(ctx, LR_ERR_UNSUPPORTED, "the backward pass supports flat per-quad colours only%s");
+  if (ctx->cfg.flags & LR_FLAG_ALPHA_THRESHOLD)
+    return fail(ctx, LR_ERR_UNSUPPORTED, "no backward pass for the alpha-threshold composite%s");
   if (!aligned(fwd_rgba, 16) || !aligned(grad_out, 16) || !aligned(grad_colors, 16))
     return fail(ctx, LR_ERR_INVALID_ARG, "fwd_rgba, grad_out and grad_colors must be 16-byte aligned%s");
   lr_view v;

@@ -190,6 +190,9 @@ struct Ws {
   const float* fwd;          // f32[H][W][4] of view 0
   float* grad_col;           // f32[Q][4] of view 0
   const uint32_t* bwd_mask;  // optional: the forward's exact-path mask of view 0
+  // alpha threshold: blend a fragment only while the pixel's transmittance is above t_min
+  // (0: off, every fragment blended)
+  float t_min;
 };
 
 // 32x32 bit-matrix transpose across a warp: lane r holds row r on entry (bit c = element

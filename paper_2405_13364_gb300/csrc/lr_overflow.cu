@@ -114,6 +114,25 @@ __device__ __forceinline__ int pow2_at_least(int n) {
 __device__ void composite_sorted(const Ws& ws, const ViewDev& V, const unsigned long long* buf, int m, int px,
                                  int py, float& cr, float& cg, float& cb, float& T, const GradPixel* gp) {
   const int lane = threadIdx.x & 31;
+  if (ws.t_min > 0.0f) {
+    // alpha threshold (forward only): whether a fragment is blended depends on the exact
+    // running product T, which the segmented scan below rounds differently, so one lane
+    // walks the fragments in order with the rasteriser's blend and stops where T <= t_min
+    if (lane == 0) {
+      for (int k = 0; k < m && T > ws.t_min; ++k) {
+        const uint32_t id = (uint32_t)buf[k];
+        float4 col;
+        unsigned long long dummy;
+        frag_eval(ws, V, (uint32_t)(V.quad_base + (id >> 1)), (int)(id & 1u), px, py, dummy, &col);
+        const float w = T * col.w;
+        cr += w * col.x; cg += w * col.y; cb += w * col.z;
+        T *= 1.0f - col.w;
+      }
+    }
+    cr = __shfl_sync(0xffffffffu, cr, 0); cg = __shfl_sync(0xffffffffu, cg, 0);
+    cb = __shfl_sync(0xffffffffu, cb, 0); T = __shfl_sync(0xffffffffu, T, 0);
+    return;
+  }
   const int seg = (m + 31) / 32;
   float sr = 0.f, sg = 0.f, sb = 0.f, sT = 1.f;
   for (int k = lane * seg; k < min(m, (lane + 1) * seg); ++k) {
@@ -243,6 +262,7 @@ __device__ void overflow_pixel(const Ws& ws, long long pid, unsigned long long* 
     const int m = min(nbuf, kOvfKeep);
     composite_sorted(ws, V, buf, m, px, py, cr, cg, cb, T, BWD ? &gp : nullptr);
     if (below <= kOvfKeep || m == 0) break;
+    if (!BWD && ws.t_min > 0.0f && !(T > ws.t_min)) break;   // alpha threshold reached
     tau = buf[m - 1];
     __syncwarp();
   }

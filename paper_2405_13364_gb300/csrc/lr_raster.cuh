@@ -51,6 +51,14 @@ constexpr int kRasterWarps = kRasterThreads / 32;
 constexpr int kOvfKeep = 480;               // fragments composited per overflow pass
 constexpr int kOvfBuf = 1024;               // per-warp overflow buffer (power of two)
 constexpr int kOvfThreads = 128;
+// alpha threshold (LR_FLAG_ALPHA_THRESHOLD, the paper's opt-in early stop, Sec. 2 "Sample
+// blending"): a pixel blends a fragment only while its transmittance is above this, i.e.
+// until its accumulated alpha reaches 1 - 1/128
+constexpr float kAlphaTMin = 1.0f / 128.0f;
+// The fp32 depth key of any fragment of a quad is at most its largest vertex 1/w times
+// this: the key is a convex combination of three vertex values evaluated with a handful
+// of roundings of relative size 2^-24 each, far inside the 2^-16 margin.
+constexpr float kKeyBoundScale = 1.0f + 1.0f / 65536.0f;
 
 // Per (triangle, half-block) record read by the fragment loop, laid out for three 16-byte
 // shared-memory loads. Edges 1 (v2->v0) and 2 (v0->v1) give the barycentric numerators
@@ -279,7 +287,10 @@ __device__ __forceinline__ float tri_key(const TriSm& T, int4 ea, int4 eb, float
   return __fadd_rn(kq.x, __fadd_rn(__fmul_rn(l1, kq.y), __fmul_rn(l2, kq.z)));
 }
 
-template <int K, bool VTX, bool BWD = false>
+// ATH: the alpha-threshold variant. Once the transmittance drops to kAlphaTMin nothing
+// more is blended and `last` stays at the key of the fragment that got it there, so the
+// misorder test below only flags fragments that belong in front of that one.
+template <int K, bool VTX, bool BWD = false, bool ATH = false>
 struct PixelState {
   // K = 1 with flat colours gathered at blend time: the colour of the fragment held in the
   // slot is loaded when it enters, so the gather overlaps the next fragment's work
@@ -299,6 +310,9 @@ struct PixelState {
     T = 1.f;
     flagged = false;
   }
+
+  // the pixel still blends (always, without the threshold)
+  __device__ __forceinline__ bool live() const { return !ATH || T > kAlphaTMin; }
 
   __device__ __forceinline__ void blend(unsigned long long key, float4 col, const ViewDev& V) {
     const uint32_t j = (uint32_t)key >> 1;
@@ -346,10 +360,12 @@ struct PixelState {
     }
     if (VTX && K == 1) {       // one slot: branch instead of selecting keys and colours
       if (x > s[0]) {          // nearer than the held fragment: blend it at once
-        blend(x, xc, V);
-        last = x;
+        if (live()) {
+          blend(x, xc, V);
+          last = x;
+        }
       } else {
-        if (s[0] != kSent) {
+        if (s[0] != kSent && live()) {
           blend(s[0], c[0], V);
           last = s[0];
         }
@@ -361,10 +377,12 @@ struct PixelState {
     if (kPrefetch) {
       const float4* cp = reinterpret_cast<const float4*>(V.col) + ((uint32_t)x >> 1);
       if (x > s[0]) {          // nearer than the held fragment: blend it at once
-        blend(x, __ldg(cp), V);
-        last = x;
+        if (live()) {
+          blend(x, __ldg(cp), V);
+          last = x;
+        }
       } else {
-        if (s[0] != kSent) {
+        if (s[0] != kSent && live()) {
           blend(s[0], c[0], V);
           last = s[0];
         }
@@ -393,7 +411,7 @@ struct PixelState {
         c[i] = take_next ? nc : (take_y ? yc : c[i]);
       }
     }
-    if (ev != kSent) {
+    if (ev != kSent && live()) {
       blend(ev, evc, V);
       last = ev;
     }
@@ -402,7 +420,7 @@ struct PixelState {
   __device__ __forceinline__ void flush(const ViewDev& V) {
 #pragma unroll
     for (int i = 0; i < K; ++i)
-      if (s[i] != kSent) blend(s[i], VTX || kPrefetch ? c[i] : make_float4(0.f, 0.f, 0.f, 0.f), V);
+      if (s[i] != kSent && live()) blend(s[i], VTX || kPrefetch ? c[i] : make_float4(0.f, 0.f, 0.f, 0.f), V);
   }
 };
 
@@ -420,8 +438,10 @@ __device__ __forceinline__ void write_pixel(const ViewDev& V, long long pidx, fl
 }
 
 // HASH: the variant that also writes the per-pixel coverage hash (a test output); the
-// others carry no code or registers for it.
-template <int K, bool VTX, bool BWD, bool HASH>
+// others carry no code or registers for it. ATH: the alpha-threshold variant (forward
+// only, no hash), which also skips candidate quads that cannot reach in front of any
+// pixel of the half-block still blending.
+template <int K, bool VTX, bool BWD, bool HASH, bool ATH = false>
 __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster(Ws ws) {
   pdl_begin();
   extern __shared__ __align__(16) unsigned char smem[];
@@ -454,7 +474,7 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
     const bool vtx_view = V.color_mode == LR_COLOR_VERTEX;
     const bool hashing = HASH && V.hash != nullptr;
 
-    PixelState<K, VTX, BWD> st;
+    PixelState<K, VTX, BWD, ATH> st;
     st.init();
     st.gp.grad = nullptr;
     st.gp.agg = agg;
@@ -469,9 +489,29 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
     unsigned long long hsh = 0;
 
     auto process = [&](int nc, uint32_t rec) {
+      bool skip = false;
+      if (ATH) {
+        // The smallest key a fragment must exceed to change any pixel of the half-block:
+        // 0 while a pixel still blends; a finished pixel needs a fragment in front of the
+        // one that finished it (keys are positive floats, so their bits order like them);
+        // pixels outside the image and pixels left to the exact path need nothing. A
+        // candidate whose largest possible key is below that is skipped: every fragment
+        // of it would be dropped.
+        const uint32_t need = (!pix_ok || st.flagged) ? 0xFFFFFFFFu : (st.live() ? 0u : (uint32_t)(st.last >> 32));
+        const uint32_t kmin = __reduce_min_sync(0xffffffffu, need);
+        if (kmin != 0u) {
+          if (lane < nc) {
+            const int4 qv = __ldg(ws.rec + 4ull * rec + 2);   // the record's four 1/w
+            const float qm = fmaxf(fmaxf(__int_as_float(qv.x), __int_as_float(qv.y)),
+                                   fmaxf(__int_as_float(qv.z), __int_as_float(qv.w)));
+            skip = __float_as_uint(qm * kKeyBoundScale) < kmin;
+          }
+          if (__all_sync(0xffffffffu, skip || lane >= nc)) return;
+        }
+      }
       // ---- 2. triangle setup and coverage masks, one quad per lane ---------------------
       uint32_t tm0 = 0, tm1 = 0;
-      if (lane < nc) {
+      if (lane < nc && !(ATH && skip)) {
         const QuadRec R = load_rec(ws.rec, rec);
         const uint32_t jl = (uint32_t)(rec - V.quad_base);
         uint32_t vsel = 0;   // per set-up triangle t: bit 8 + t, and its corners 1, 2 at bits 4t
@@ -660,9 +700,9 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
 // parallel.
 #define LR_DEFINE_RASTER(KK)                                                                  \
   namespace lr {                                                                              \
-  template <bool VTX, bool BWD, bool HASH>                                                    \
+  template <bool VTX, bool BWD, bool HASH, bool ATH = false>                                  \
   static cudaError_t raster_attr_##KK() {                                                     \
-    return cudaFuncSetAttribute(k_raster<KK, VTX, BWD, HASH>,                                 \
+    return cudaFuncSetAttribute(k_raster<KK, VTX, BWD, HASH, ATH>,                            \
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,                  \
                                 (int)raster_smem_bytes(VTX, BWD));                            \
   }                                                                                           \
@@ -672,6 +712,8 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
     if (e == cudaSuccess) e = raster_attr_##KK<false, true, false>();                         \
     if (e == cudaSuccess) e = raster_attr_##KK<false, false, true>();                         \
     if (e == cudaSuccess) e = raster_attr_##KK<true, false, true>();                          \
+    if (e == cudaSuccess) e = raster_attr_##KK<false, false, false, true>();                  \
+    if (e == cudaSuccess) e = raster_attr_##KK<true, false, false, true>();                   \
     if (e != cudaSuccess) return e;                                                           \
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_flat, k_raster<KK, false, false, false>, \
                                                       kRasterThreads, raster_smem_bytes(false)); \
@@ -682,7 +724,8 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_vtx, k_raster<KK, true, false, false>, \
                                                          kRasterThreads, raster_smem_bytes(true)); \
   }                                                                                           \
-  /* mode: 0 flat colours, 1 colours in the sorter, 2 backward; + 4: coverage hash */        \
+  /* mode: 0 flat colours, 1 colours in the sorter, 2 backward; + 4: coverage hash;        \
+     + 8: alpha threshold (modes 8 and 9 only) */                                             \
   cudaError_t launch_raster_##KK(int mode, const Ws& ws, int grid, cudaStream_t st) {         \
     const size_t sf = raster_smem_bytes(false), sv = raster_smem_bytes(true);                 \
     /* a plain launch: with programmatic serialisation the persistent CTAs, placed early  \
@@ -692,6 +735,8 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
       case 2: k_raster<KK, false, true, false><<<grid, kRasterThreads, raster_smem_bytes(false, true), st>>>(ws); break; \
       case 4: k_raster<KK, false, false, true><<<grid, kRasterThreads, sf, st>>>(ws); break;  \
       case 5: k_raster<KK, true, false, true><<<grid, kRasterThreads, sv, st>>>(ws); break;   \
+      case 8: k_raster<KK, false, false, false, true><<<grid, kRasterThreads, sf, st>>>(ws); break; \
+      case 9: k_raster<KK, true, false, false, true><<<grid, kRasterThreads, sv, st>>>(ws); break; \
       default: k_raster<KK, false, false, false><<<grid, kRasterThreads, sf, st>>>(ws); break; \
     }                                                                                         \
     return cudaGetLastError();                                                                \
