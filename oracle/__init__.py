@@ -10,6 +10,8 @@ Functions (each follows the definition stated in ``lr_oracle.c``):
   setup(scene)                 per-quad cull status, snapped X/Y, q = 1/w, pixel AABB
   render(scene)                fp32 image, per-pixel fragment count and coverage hash,
                                8-bit image, the fp64 composite of the same fragment order
+  render_msaa(scene, offsets)  multisampled image: the mean of the exact images of several
+                               sample positions per pixel (offsets from the centre)
   render_pixels(scene, xs, ys) the same quantities for selected pixels only
   render_threshold(scene, t)   the opt-in lossy alpha-threshold composite (front to back,
                                a fragment blended only while transmittance > t)
@@ -43,6 +45,7 @@ class _Scene(ctypes.Structure):
         ("colors", ctypes.c_void_p), ("color_mode", ctypes.c_int32),
         ("view_proj", ctypes.c_void_p), ("near_z", ctypes.c_float), ("far_z", ctypes.c_float),
         ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+        ("sample_x", ctypes.c_int32), ("sample_y", ctypes.c_int32),
     ]
 
 
@@ -127,7 +130,7 @@ def _ptr(a):
 class _Bound:
     """Keeps contiguous copies alive while the C call runs."""
 
-    def __init__(self, scene, colors=None):
+    def __init__(self, scene, colors=None, sample=(128, 128)):
         self.pos = np.ascontiguousarray(scene.positions, np.float32)
         self.idx = None if scene.indices is None else np.ascontiguousarray(scene.indices, np.uint32)
         self.col = np.ascontiguousarray(scene.colors if colors is None else colors, np.float32)
@@ -135,7 +138,7 @@ class _Bound:
         q = self.idx.shape[0] if self.idx is not None else self.pos.shape[0] // 4
         self.s = _Scene(_ptr(self.pos), self.pos.shape[0], _ptr(self.idx), q, _ptr(self.col),
                         int(scene.color_mode), _ptr(self.m), float(scene.near), float(scene.far),
-                        int(scene.width), int(scene.height))
+                        int(scene.width), int(scene.height), int(sample[0]), int(sample[1]))
         self.num_quads = q
 
 
@@ -156,9 +159,11 @@ def setup(scene):
     return dict(status=status, X=X, Y=Y, q=qq, bbox=bbox)
 
 
-def render(scene, nthreads: int = 0, want64: bool = False):
+def render(scene, nthreads: int = 0, want64: bool = False, sample=(128, 128)):
+    """sample: the position in each pixel, in 1/256 px from its top-left corner, whose
+    coverage makes the image ((128, 128): the pixel centre)."""
     lib = _load()
-    b = _Bound(scene)
+    b = _Bound(scene, sample=sample)
     H, W = scene.height, scene.width
     rgba = np.zeros((H, W, 4), np.float32)
     count = np.zeros((H, W), np.uint32)
@@ -176,6 +181,32 @@ def render(scene, nthreads: int = 0, want64: bool = False):
     if want64:
         out["rgba64"] = rgba64
     return out
+
+
+# Sample offsets from the pixel centre, in 1/256 px (x right, y down). 4 samples: a grid
+# rotated so that each sample has its own row and column, offsets (+-1/8, +-3/8) px. 16
+# samples: one per row and column of a 16 x 16 sub-grid (cells 1/16 px), the column of row
+# i being (5 i + 3) mod 16.
+MSAA_OFFSETS = {
+    4: [(-32, -96), (96, -32), (-96, 32), (32, 96)],
+    16: [(16 * ((5 * i + 3) % 16) - 120, 16 * i - 120) for i in range(16)],
+}
+
+
+def render_msaa(scene, offsets=4, nthreads: int = 0):
+    """Multisampled exact OIT: for every sample offset (dx, dy) the exact image with
+    coverage, depth and colour taken at (256 px + 128 + dx, 256 py + 128 + dy), then the
+    per-pixel mean (fp32 sum in sample order, divided by the sample count). offsets: a
+    list of (dx, dy) or a sample count with a default pattern (MSAA_OFFSETS)."""
+    if isinstance(offsets, int):
+        offsets = MSAA_OFFSETS[offsets]
+    acc = None
+    samples = []
+    for dx, dy in offsets:
+        img = render(scene, nthreads, sample=(128 + dx, 128 + dy))["rgba"]
+        samples.append(img)
+        acc = img.copy() if acc is None else (acc + img).astype(np.float32)
+    return (acc / np.float32(len(offsets))).astype(np.float32), samples
 
 
 def render_pixels(scene, xs, ys, nthreads: int = 0):

@@ -81,8 +81,9 @@ def snapped_quads(scene):
     return out
 
 
-def render(scene):
-    """Returns (rgba f32[H][W][4], count u32[H][W], hash u64[H][W])."""
+def render(scene, sample=(128, 128)):
+    """Returns (rgba f32[H][W][4], count u32[H][W], hash u64[H][W]); sample is the position
+    in each pixel (1/256 px from its top-left corner) whose coverage is tested."""
     W, H = scene.width, scene.height
     quads = snapped_quads(scene)
     rgba = np.zeros((H, W, 4), np.float32)
@@ -91,7 +92,7 @@ def render(scene):
     cols = np.asarray(scene.colors, np.float32)
     for py in range(H):
         for px in range(W):
-            Px, Py = 256 * px + 128, 256 * py + 128
+            Px, Py = 256 * px + sample[0], 256 * py + sample[1]
             frags = []
             for j, qd in enumerate(quads):
                 if qd is None:

@@ -24,7 +24,8 @@
  *                   (8 fractional bits, round half to even); q = 1/w.
  *   O.5 triangles   T0 = (v0,v1,v2), T1 = (v0,v2,v3); int64 doubled area; negative
  *                   area -> swap v1,v2; zero area -> no coverage.
- *   O.6 coverage    centre (256px+128, 256py+128); edge a->b value
+ *   O.6 coverage    centre (256px+128, 256py+128) (or another sample position of the
+ *                   pixel, for multisampling); edge a->b value
  *                   E = (Xb-Xa)(Py-Ya) - (Yb-Ya)(Px-Xa); owned iff dy<0 || (dy==0 && dx>0);
  *                   covered iff every edge has E>0 or (E==0 and owned).
  *   O.8 depth key   inv = 1/(float)A; l1 = (float)E_20 * inv; l2 = (float)E_01 * inv;
@@ -70,6 +71,10 @@ typedef struct {
   const float* view_proj;   /* [16], row-major */
   float near_z, far_z;
   int32_t width, height;
+  /* where in each pixel the sample lies, in 1/256 px from the pixel's top-left corner:
+   * (128, 128) is the pixel centre of O.6; a multisampled image (MSAA) is the mean of
+   * the images of several sample positions */
+  int32_t sample_x, sample_y;
 } or_scene;
 
 typedef struct {
@@ -155,8 +160,9 @@ static void setup_quad(const or_scene* s, int64_t j, or_quad* out) {
     if (out->Y[k] < ymin) ymin = out->Y[k];
     if (out->Y[k] > ymax) ymax = out->Y[k];
   }
-  int32_t px0 = ceil_div256((int64_t)xmin - 128), px1 = floor_div256((int64_t)xmax - 128);
-  int32_t py0 = ceil_div256((int64_t)ymin - 128), py1 = floor_div256((int64_t)ymax - 128);
+  /* pixels whose sample position lies in the quad's box */
+  int32_t px0 = ceil_div256((int64_t)xmin - s->sample_x), px1 = floor_div256((int64_t)xmax - s->sample_x);
+  int32_t py0 = ceil_div256((int64_t)ymin - s->sample_y), py1 = floor_div256((int64_t)ymax - s->sample_y);
   if (px0 < 0) px0 = 0;
   if (py0 < 0) py0 = 0;
   if (px1 > s->width - 1) px1 = s->width - 1;
@@ -218,10 +224,10 @@ static void make_tri(const or_quad* qd, int t, const or_scene* s, or_tri* tri) {
     if (tri->Y[k] < ymin) ymin = tri->Y[k];
     if (tri->Y[k] > ymax) ymax = tri->Y[k];
   }
-  tri->px0 = ceil_div256((int64_t)xmin - 128);
-  tri->px1 = floor_div256((int64_t)xmax - 128);
-  tri->py0 = ceil_div256((int64_t)ymin - 128);
-  tri->py1 = floor_div256((int64_t)ymax - 128);
+  tri->px0 = ceil_div256((int64_t)xmin - s->sample_x);
+  tri->px1 = floor_div256((int64_t)xmax - s->sample_x);
+  tri->py0 = ceil_div256((int64_t)ymin - s->sample_y);
+  tri->py1 = floor_div256((int64_t)ymax - s->sample_y);
   if (tri->px0 < 0) tri->px0 = 0;
   if (tri->py0 < 0) tri->py0 = 0;
   if (tri->px1 > s->width - 1) tri->px1 = s->width - 1;
@@ -235,7 +241,7 @@ static int64_t edge_value(int32_t xa, int32_t ya, int32_t xb, int32_t yb, int64_
 /* Returns 1 and fills key / rgba if pixel (px, py) is covered by the triangle. */
 static int shade(const or_scene* s, const or_tri* tri, int64_t j, int32_t px, int32_t py,
                  float* key, float rgba[4]) {
-  int64_t Px = 256 * (int64_t)px + 128, Py = 256 * (int64_t)py + 128;
+  int64_t Px = 256 * (int64_t)px + s->sample_x, Py = 256 * (int64_t)py + s->sample_y;
   int64_t e0 = edge_value(tri->X[1], tri->Y[1], tri->X[2], tri->Y[2], Px, Py);
   int64_t e1 = edge_value(tri->X[2], tri->Y[2], tri->X[0], tri->Y[0], Px, Py);
   int64_t e2 = edge_value(tri->X[0], tri->Y[0], tri->X[1], tri->Y[1], Px, Py);

@@ -5,6 +5,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_pins as pins
+from tests import test_oracle_msaa as mpins
 from tests import test_oracle_threshold as tpins
 
 MUTANTS = {
@@ -47,6 +48,10 @@ MUTANTS = {
     # alpha threshold: fragments weighted by their own alpha only (no transmittance)
     "threshold_no_transmittance": ("float w = T * a;", "float w = a;",
                                    [tpins.test_stack_closed_form]),
+    # multisampling: coverage still tested at the pixel centre
+    "sample_position_ignored": ("int64_t Px = 256 * (int64_t)px + s->sample_x, Py = 256 * (int64_t)py + s->sample_y;",
+                                "int64_t Px = 256 * (int64_t)px + 128, Py = 256 * (int64_t)py + 128;",
+                                [mpins.test_partial_coverage_closed_form]),
     # near plane ignored
     "no_near_cull": ("} else if (!(w >= s->near_z && w <= s->far_z)) {",
                      "} else if (!(w <= s->far_z)) {",
@@ -60,6 +65,8 @@ def _call(test):
         test(False, 0)
     elif test is tpins.test_stack_closed_form:
         test(0.5, 7)
+    elif test is mpins.test_partial_coverage_closed_form:
+        test(4)
     else:
         test()
 
