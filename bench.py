@@ -554,6 +554,30 @@ def run_gpu(args):
                            "max_abs_deviation_from_exact": round(dev_max, 6), "bound": 1 / 128}
         ra.close()
 
+    # ---- multisampling (4 samples per pixel, every sample an exact composite) ------------
+    msaa = None
+    if world == 1:
+        rm = P.Renderer(sorter_k=args.k, carry_colors=carry)
+        rm.render_msaa(ds, W, H, samples=4)           # sizes the workspace
+        stm = rm.stats()
+        for _ in range(args.warmup):
+            rm.render_msaa(ds, W, H, samples=4, check=False)
+        m_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(10)]
+        torch.cuda.synchronize()
+        for i, (a0, a1) in enumerate(m_ev):
+            flush.fill_(i & 0xFF)
+            a0.record(stream)
+            rm.render_msaa(ds, W, H, samples=4, check=False)
+            a1.record(stream)
+        torch.cuda.synchronize()
+        m_ms = sum(a0.elapsed_time(a1) for a0, a1 in m_ev) / len(m_ev)
+        msaa = {"samples": 4, "ms_per_frame": round(m_ms, 4),
+                "sample_fragments_per_frame": int(stm["fragments"]),
+                "gfrag_s": round(int(stm["fragments"]) / (m_ms * 1e-3) / 1e9, 2),
+                "vs_single_sample_ms": round(m_ms / ms_step, 3)}
+        rm.close()
+
     # ---- CPU oracle on a bounded sample: full frames for ~10 s ---------------------------
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -601,6 +625,7 @@ def run_gpu(args):
         "binning_hbm": None,
         "overflow_pixel_fraction": overflow_frac,
         "alpha_threshold": alpha_threshold,
+        "msaa": msaa,
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 3), "unit": "Gfrag/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4),

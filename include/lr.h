@@ -282,6 +282,35 @@ lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* camera, int3
                             int32_t height, float* out_rgba, int32_t* device_status,
                             lr_stream stream);
 
+/* ---- multisampling ------------------------------------------------------------------
+ * (The paper's prototype has no anti-aliasing; Sec. 4, "Future work", names 4x and 16x
+ * multisample anti-aliasing as an extension that mainly changes the coverage and blending
+ * phases of the raster stage.) lr_render_msaa renders one frame with n_samples sample
+ * positions per pixel. Every sample gets the exact composite of the fragments covering it
+ * (coverage, depth key and colour taken at the sample, same order and tie rule as
+ * lr_render); the output pixel is the mean of its samples (fp32 sum in sample order,
+ * divided by n_samples). The samples are the views of one batched render (every stage
+ * launched once for all samples), followed by one resolve kernel.
+ *  - quads, camera: as for lr_render.
+ *  - n_samples: 1..16.
+ *  - sample_offsets: host int32[n_samples][2], the offsets (dx, dy) of the samples from the
+ *    pixel centre in 1/256 px (x right, y down), each in [-127, 127]; or NULL for the default
+ *    pattern of n_samples = 4 (a rotated grid: offsets (+-1/8, +-3/8) px, one sample per row
+ *    and column of a 4x4 sub-grid) or 16 (one sample per row and column of a 16x16 sub-grid,
+ *    row i, counted from the top, in column (5 i + 3) mod 16).
+ *  - out_rgba: device f32[H][W][4], 16-byte aligned.
+ *  - workspace: device, 256-byte aligned, at least lr_workspace_size_msaa() bytes: the
+ *    per-sample images (16 B per pixel and sample) followed by the batch's workspace.
+ *  - Returns LR_ERR_INVALID_ARG for n_samples outside 1..16, NULL offsets with n_samples
+ *    other than 4 or 16, an offset outside [-127, 127] or bad pointers; LR_ERR_OOM when the
+ *    workspace is too small; otherwise as lr_render. lr_get_stats reports the samples as
+ *    views (fragments summed over the samples). */
+lr_status lr_workspace_size_msaa(const lr_ctx* ctx, int64_t num_quads, int32_t width, int32_t height,
+                                 int32_t n_samples, size_t* out_bytes);
+lr_status lr_render_msaa(lr_ctx* ctx, const lr_quads* quads, const lr_camera* camera, int32_t width,
+                         int32_t height, int32_t n_samples, const int32_t* sample_offsets, float* out_rgba,
+                         void* workspace, size_t workspace_bytes, lr_stream stream);
+
 /* ---- serving: continuous batching of render requests ------------------------------
  * (Not in the paper; it serves the single-frame pipeline.) A host thread keeps
  * num_slots batches in flight, each on its own CUDA stream with its own device workspace

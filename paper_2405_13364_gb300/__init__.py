@@ -180,6 +180,29 @@ class Renderer:
         self.render_views([self.view_struct(scene, width, height, out)], stream, check)
         return out
 
+    def render_msaa(self, scene: DeviceScene, width: int, height: int, samples: int = 4, offsets=None,
+                    stream=None, check: bool = True) -> torch.Tensor:
+        """Multisampled render (lr_render_msaa): every sample position of a pixel gets its own
+        exact composite and the pixel is their mean. offsets: None for the default pattern of
+        4 or 16 samples, else samples pairs (dx, dy) from the pixel centre in 1/256 px."""
+        stream = torch.cuda.current_stream(self.device) if stream is None else stream
+        out = torch.empty((height, width, 4), dtype=torch.float32, device=self.device)
+        need = B.lr_workspace_size_msaa(self.ctx, scene.num_quads, width, height, samples)
+        for _ in range(3):
+            ptr, nbytes = self.workspace(need)
+            B.lr_render_msaa(self.ctx, scene.quads_struct(), scene.camera_struct(), width, height, samples,
+                             offsets, _ptr(out), ptr, nbytes, stream.cuda_stream)
+            if not check:
+                return out
+            st = B.lr_get_stats(self.ctx, raise_on_error=False)
+            if st.status == LR_ERR_OVERFLOW:      # more bin references than the workspace held
+                need = nbytes + 20 * int(st.bin_refs) + (1 << 20)
+                continue
+            if st.status != LR_OK:
+                raise LrError(st.status, B.lr_last_error(self.ctx))
+            return out
+        raise LrError(LR_ERR_OVERFLOW, "bin references kept exceeding the workspace")
+
     def render_batch(self, items, stream=None, check: bool = True, **outputs):
         """items: list of (DeviceScene, width, height). One launch per stage for all."""
         outs = [self.make_outputs(w, h, **outputs) for _, w, h in items]

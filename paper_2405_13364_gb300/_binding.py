@@ -141,6 +141,11 @@ _SIGNATURES = {
     "lr_graph_destroy": (ctypes.c_int, [_P]),
     "lr_render_noalloc": (ctypes.c_int, [ctypes.POINTER(lr_quads), ctypes.POINTER(lr_camera),
                                          ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
+    "lr_workspace_size_msaa": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+    "lr_render_msaa": (ctypes.c_int, [_P, ctypes.POINTER(lr_quads), ctypes.POINTER(lr_camera),
+                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, _P,
+                                      ctypes.c_size_t, _P]),
 }
 
 _lib = None
@@ -222,6 +227,24 @@ def lr_render_batch(ctx, views, workspace: int, workspace_bytes: int, stream: in
     arr = (lr_view * len(views))(*views)
     _check(ctx, load().lr_render_batch(ctx, len(views), arr, workspace, workspace_bytes, stream),
            "lr_render_batch")
+
+
+def lr_workspace_size_msaa(ctx, num_quads: int, width: int, height: int, n_samples: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(ctx, load().lr_workspace_size_msaa(ctx, num_quads, width, height, n_samples, ctypes.byref(n)),
+           "lr_workspace_size_msaa")
+    return n.value
+
+
+def lr_render_msaa(ctx, quads: lr_quads, camera: lr_camera, width: int, height: int, n_samples: int,
+                   offsets, out_rgba: int, workspace: int, workspace_bytes: int, stream: int):
+    """offsets: None (the default pattern) or a sequence of (dx, dy) in 1/256 px."""
+    arr = None
+    if offsets is not None:
+        flat = [int(v) for xy in offsets for v in xy]
+        arr = (ctypes.c_int32 * len(flat))(*flat)
+    _check(ctx, load().lr_render_msaa(ctx, ctypes.byref(quads), ctypes.byref(camera), width, height, n_samples,
+                                      arr, out_rgba, workspace, workspace_bytes, stream), "lr_render_msaa")
 
 
 def lr_render_backward(ctx, quads: lr_quads, camera: lr_camera, width: int, height: int,

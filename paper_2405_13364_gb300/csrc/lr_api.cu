@@ -684,6 +684,123 @@ extern "C" lr_status lr_render(lr_ctx* ctx, const lr_quads* quads, const lr_came
   return lr_render_batch(ctx, 1, &v, workspace, workspace_bytes, stream);
 }
 
+// ---- multisampling --------------------------------------------------------------------
+
+namespace lr {
+
+constexpr int kMaxSamples = 16;
+
+// default sample patterns, offsets from the pixel centre in 1/256 px: 4 samples on a grid
+// rotated so that each has its own row and column (offsets +-1/8 and +-3/8 px); 16 samples
+// one per row and column of a 16x16 sub-grid, row i (from the top) in column (5 i + 3) mod 16
+static void default_samples(int n, int off[][2]) {
+  if (n == 4) {
+    static const int r4[4][2] = {{-32, -96}, {96, -32}, {-96, 32}, {32, 96}};
+    for (int i = 0; i < 4; ++i) { off[i][0] = r4[i][0]; off[i][1] = r4[i][1]; }
+  } else {
+    for (int i = 0; i < 16; ++i) {
+      off[i][0] = 16 * ((5 * i + 3) % 16) - 120;
+      off[i][1] = 16 * i - 120;
+    }
+  }
+}
+
+// out = (sum of the n sample images, in sample order) / n, per channel in fp32
+__global__ void k_resolve(const float4* samples, int n, long long npix, float4* out) {
+  pdl_begin();
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= npix) return;
+  float4 acc = samples[i];
+  for (int s = 1; s < n; ++s) {
+    const float4 v = samples[(long long)s * npix + i];
+    acc.x = __fadd_rn(acc.x, v.x);
+    acc.y = __fadd_rn(acc.y, v.y);
+    acc.z = __fadd_rn(acc.z, v.z);
+    acc.w = __fadd_rn(acc.w, v.w);
+  }
+  const float fn = (float)n;
+  out[i] = make_float4(__fdiv_rn(acc.x, fn), __fdiv_rn(acc.y, fn), __fdiv_rn(acc.z, fn), __fdiv_rn(acc.w, fn));
+}
+
+static size_t msaa_image_bytes(int n, int width, int height) {
+  return align256(sizeof(float4) * (size_t)width * (size_t)height * (size_t)n);
+}
+
+}  // namespace lr
+
+extern "C" lr_status lr_workspace_size_msaa(const lr_ctx* ctx, int64_t num_quads, int32_t width, int32_t height,
+                                            int32_t n_samples, size_t* out_bytes) {
+  if (!ctx || !out_bytes || num_quads < 0 || width <= 0 || height <= 0) return LR_ERR_INVALID_ARG;
+  if (n_samples < 1 || n_samples > kMaxSamples) return LR_ERR_INVALID_ARG;
+  if (width > ctx->cfg.max_width || height > ctx->cfg.max_height) return LR_ERR_TOO_LARGE;
+  std::vector<long long> Q(n_samples, num_quads);
+  std::vector<int> W(n_samples, width), H(n_samples, height);
+  Layout L = make_layout(n_samples, Q.data(), W.data(), H.data());
+  if (L.total_quads > 0x7FFFFFFFLL || L.total_pix > 0xFFFFFFFFLL) return LR_ERR_TOO_LARGE;
+  *out_bytes = msaa_image_bytes(n_samples, width, height) + bytes_for_refs(L, default_refs(L, ctx->cfg.ref_factor));
+  return LR_OK;
+}
+
+extern "C" lr_status lr_render_msaa(lr_ctx* ctx, const lr_quads* quads, const lr_camera* camera, int32_t width,
+                                    int32_t height, int32_t n_samples, const int32_t* sample_offsets, float* out_rgba,
+                                    void* workspace, size_t workspace_bytes, lr_stream stream) {
+  if (!ctx) return LR_ERR_INVALID_ARG;
+  if (!quads || !camera || !out_rgba) return fail(ctx, LR_ERR_INVALID_ARG, "null quads, camera or output%s");
+  if (n_samples < 1 || n_samples > kMaxSamples) return fail(ctx, LR_ERR_INVALID_ARG, "n_samples must be 1..16%s");
+  if (!sample_offsets && n_samples != 4 && n_samples != 16)
+    return fail(ctx, LR_ERR_INVALID_ARG, "default sample patterns exist for 4 and 16 samples only%s");
+  if (width <= 0 || height <= 0) return fail(ctx, LR_ERR_INVALID_ARG, "width and height must be positive%s");
+  if (!aligned(out_rgba, 16)) return fail(ctx, LR_ERR_INVALID_ARG, "out_rgba must be 16-byte aligned%s");
+  if (!workspace || !aligned(workspace, 256))
+    return fail(ctx, LR_ERR_INVALID_ARG, "workspace must be non-null and 256-byte aligned%s");
+  int off[kMaxSamples][2];
+  if (sample_offsets) {
+    for (int i = 0; i < n_samples; ++i) {
+      off[i][0] = sample_offsets[2 * i];
+      off[i][1] = sample_offsets[2 * i + 1];
+      if (off[i][0] < -127 || off[i][0] > 127 || off[i][1] < -127 || off[i][1] > 127)
+        return fail(ctx, LR_ERR_INVALID_ARG, "sample offsets must lie in [-127, 127]%s");
+    }
+  } else {
+    default_samples(n_samples, off);
+  }
+  const size_t img = msaa_image_bytes(n_samples, width, height);
+  if (workspace_bytes <= img) return fail(ctx, LR_ERR_OOM, "workspace too small (see lr_workspace_size_msaa)%s");
+  float4* samples = static_cast<float4*>(workspace);
+  const long long npix = (long long)width * height;
+  std::vector<lr_view> views(n_samples);
+  for (int i = 0; i < n_samples; ++i) {
+    lr_view& v = views[i];
+    memset(&v, 0, sizeof(v));
+    v.quads = *quads;
+    v.camera = *camera;
+    v.width = width;
+    v.height = height;
+    v.target.rgba = reinterpret_cast<float*>(samples + (long long)i * npix);
+  }
+  void* ws = static_cast<char*>(workspace) + img;
+  Prepared P;
+  lr_status s = prepare(ctx, n_samples, views.data(), ws, workspace_bytes - img, &P);
+  if (s != LR_OK) return s;
+  for (int i = 0; i < n_samples; ++i) {
+    P.vd[i].sub_x = off[i][0];
+    P.vd[i].sub_y = off[i][1];
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  const bool timed = (ctx->cfg.flags & LR_FLAG_TIMING) != 0;
+  s = launch_sequence(ctx, P, st, nullptr, timed, nullptr);
+  if (s != LR_OK) return s;
+  const bool pdl = (ctx->cfg.flags & LR_FLAG_NO_PDL) == 0;
+  e = launch_pdl(pdl, k_resolve, dim3((unsigned)((npix + 255) / 256)), dim3(256), 0, st,
+                 static_cast<const float4*>(samples), (int)n_samples, npix, reinterpret_cast<float4*>(out_rgba));
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "resolve launch");
+  remember_last(ctx, P, st, ws, timed);
+  return LR_OK;
+}
+
 extern "C" lr_status lr_get_stats(lr_ctx* ctx, lr_stats* stats) {
   if (!ctx) return LR_ERR_INVALID_ARG;
   if (!ctx->have_last) return fail(ctx, LR_ERR_INVALID_ARG, "no render issued on this context%s");

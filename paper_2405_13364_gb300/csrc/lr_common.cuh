@@ -76,6 +76,9 @@ struct ViewDev {
   int nbx, nby;              // bins per row / column
   int bin_base;              // first bin of this view in the flattened bin space
   int chunk_base;            // first binning chunk (kChunkQuads quads) of this view
+  int sub_x, sub_y;          // multisampling: the view's sample offset from the pixel centre
+                             // (1/256 px), subtracted from the snapped vertices, so that the
+                             // pixel-centre tests of every later stage test the sample
 };
 
 // Up to kViewsPerLaunch view descriptors passed by value to a kernel, which writes them to

@@ -99,8 +99,11 @@ __global__ __launch_bounds__(256) void k_setup(Ws ws) {
         if (!(fabsf(sx) <= kGuardPx && fabsf(sy) <= kGuardPx)) {
           why = kGuard;
         } else {
-          X[k] = __float2int_rn(__fmul_rn(sx, 256.0f));
-          Y[k] = __float2int_rn(__fmul_rn(sy, 256.0f));
+          // (minus the sample offset of a multisampled view: edge values, the depth key and
+          // the colour weights are differences of vertex positions and the tested point, so
+          // moving the vertices by -d tests the point centre + d exactly)
+          X[k] = __float2int_rn(__fmul_rn(sx, 256.0f)) - V.sub_x;
+          Y[k] = __float2int_rn(__fmul_rn(sy, 256.0f)) - V.sub_y;
           q[k] = qk;
         }
       }
