@@ -46,6 +46,7 @@ class _Scene(ctypes.Structure):
         ("view_proj", ctypes.c_void_p), ("near_z", ctypes.c_float), ("far_z", ctypes.c_float),
         ("width", ctypes.c_int32), ("height", ctypes.c_int32),
         ("sample_x", ctypes.c_int32), ("sample_y", ctypes.c_int32),
+        ("light", ctypes.c_float * 4),
     ]
 
 
@@ -138,7 +139,8 @@ class _Bound:
         q = self.idx.shape[0] if self.idx is not None else self.pos.shape[0] // 4
         self.s = _Scene(_ptr(self.pos), self.pos.shape[0], _ptr(self.idx), q, _ptr(self.col),
                         int(scene.color_mode), _ptr(self.m), float(scene.near), float(scene.far),
-                        int(scene.width), int(scene.height), int(sample[0]), int(sample[1]))
+                        int(scene.width), int(scene.height), int(sample[0]), int(sample[1]),
+                        (ctypes.c_float * 4)(*(getattr(scene, "light", None) or (0.0, 0.0, 0.0, 0.0))))
         self.num_quads = q
 
 

@@ -34,6 +34,10 @@
  *   O.9 order       back to front = ascending (key, quad, triangle).
  *   O.10 colour     flat per quad, or perspective-correct per-vertex
  *                   sum(l_k q_k c_k) / sum(l_k q_k).
+ *   lit colour      (simple lighting: per-vertex normals, one directional light) the
+ *                   perspective-correct base RGBA as above; the normal's direction
+ *                   n = sum(l_k q_k n_k); RGB scaled by amb + (1 - amb) |n.L| / (|n| |L|)
+ *                   (two-sided Lambert plus ambient, 0 for a zero normal); alpha unlit.
  *   O.11 composite  C = a c + (1-a) C, A = a + (1-a) A, from black transparent.
  *   O.12 8-bit      rint(clamp(v,0,1) * 255).
  *   O.13 backward   fp64 gradient of the composite w.r.t. flat per-quad RGBA.
@@ -67,7 +71,8 @@ typedef struct {
   const uint32_t* indices;  /* [Q][4] or NULL: quad q uses 4q..4q+3 */
   int64_t num_quads;
   const float* colors;      /* flat [Q][4] or per-vertex [V][4], straight RGBA */
-  int32_t color_mode;       /* 0 flat, 1 per-vertex */
+  int32_t color_mode;       /* 0 flat, 1 per-vertex, 2 per-vertex lit: [V][8] = RGBA, normal
+                               xyz, unused */
   const float* view_proj;   /* [16], row-major */
   float near_z, far_z;
   int32_t width, height;
@@ -75,6 +80,8 @@ typedef struct {
    * (128, 128) is the pixel centre of O.6; a multisampled image (MSAA) is the mean of
    * the images of several sample positions */
   int32_t sample_x, sample_y;
+  /* lit colours: direction toward the light (world space, any length) and the ambient term */
+  float light[4];
 } or_scene;
 
 typedef struct {
@@ -262,13 +269,27 @@ static int shade(const or_scene* s, const or_tri* tri, int64_t j, int32_t px, in
     /* perspective-correct: weights l_k q_k, evaluated in double and rounded */
     double l[3] = {(double)e0 / (double)tri->A, (double)e1 / (double)tri->A,
                    (double)e2 / (double)tri->A};
-    double wsum = 0.0, acc[4] = {0, 0, 0, 0};
+    const int stride = s->color_mode == 2 ? 8 : 4;
+    double wsum = 0.0, acc[4] = {0, 0, 0, 0}, n[3] = {0, 0, 0};
     for (int k = 0; k < 3; ++k) {
       double wk = l[k] * (double)tri->q[k];
       wsum += wk;
-      for (int c = 0; c < 4; ++c) acc[c] += wk * (double)s->colors[tri->vid[k] * 4 + c];
+      const float* ck = s->colors + tri->vid[k] * stride;
+      for (int c = 0; c < 4; ++c) acc[c] += wk * (double)ck[c];
+      if (s->color_mode == 2)
+        for (int c = 0; c < 3; ++c) n[c] += wk * (double)ck[4 + c];
     }
-    for (int c = 0; c < 4; ++c) rgba[c] = (float)(acc[c] / wsum);
+    double shade_f = 1.0;
+    if (s->color_mode == 2) {
+      double L[3] = {s->light[0], s->light[1], s->light[2]};
+      double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+      double ll = sqrt(L[0] * L[0] + L[1] * L[1] + L[2] * L[2]);
+      double lam = (nn > 0.0 && ll > 0.0) ? fabs(n[0] * L[0] + n[1] * L[1] + n[2] * L[2]) / (nn * ll) : 0.0;
+      double amb = s->light[3];
+      shade_f = amb + (1.0 - amb) * lam;
+    }
+    for (int c = 0; c < 3; ++c) rgba[c] = (float)(acc[c] / wsum * shade_f);
+    rgba[3] = (float)(acc[3] / wsum);
   }
   return 1;
 }

@@ -18,6 +18,7 @@ import numpy as np
 
 COLOR_FLAT = 0
 COLOR_VERTEX = 1
+COLOR_LIT = 2       # per-vertex [V][8]: straight RGBA, unit normal xyz, unused
 
 # Half-height (world units) of a layer of the stacked-layer generator, calibrated so
 # that 32 layers at view depths 2.0, 2.5, ..., 17.5 give a mean depth complexity of
@@ -49,6 +50,7 @@ class Scene:
     width: int
     height: int
     name: str = ""
+    light: tuple | None = None   # lit colours: (x, y, z) toward the light (world), ambient
 
     @property
     def num_quads(self) -> int:
@@ -162,6 +164,7 @@ def wavy_layers(width: int = 1920, height: int = 1080, layers: int = 32, nx: int
     ys = np.linspace(-half_h, half_h, ny + 1)
     gx, gy = np.meshgrid(xs, ys)  # [ny+1][nx+1]
     verts = []
+    normals = []
     for k in range(layers):
         lr = np.random.default_rng(k)
         kmag = lr.uniform(0.5, 3.0, 4)
@@ -172,6 +175,16 @@ def wavy_layers(width: int = 1920, height: int = 1080, layers: int = 32, nx: int
             disp += amplitude * np.sin(kmag[i] * (np.cos(ang[i]) * gx + np.sin(ang[i]) * gy) + phi[i])
         z = -(d0 + dz * k) + disp
         verts.append(np.stack([gx, gy, z], axis=-1).reshape(-1, 3))
+        if color_mode == COLOR_LIT:
+            # the displaced surface's unit normal (-dz/dx, -dz/dy, 1) / norm
+            dzx = np.zeros_like(gx)
+            dzy = np.zeros_like(gx)
+            for i in range(4):
+                c = amplitude * kmag[i] * np.cos(kmag[i] * (np.cos(ang[i]) * gx + np.sin(ang[i]) * gy) + phi[i])
+                dzx += c * np.cos(ang[i])
+                dzy += c * np.sin(ang[i])
+            nrm = np.stack([-dzx, -dzy, np.ones_like(gx)], axis=-1).reshape(-1, 3)
+            normals.append(nrm / np.linalg.norm(nrm, axis=1, keepdims=True))
     pos = np.concatenate(verts).astype(np.float32)
     nvl = (nx + 1) * (ny + 1)
     iy, ix = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
@@ -179,12 +192,19 @@ def wavy_layers(width: int = 1920, height: int = 1080, layers: int = 32, nx: int
     quad = np.stack([base, base + 1, base + nx + 2, base + nx + 1], axis=1)
     idx = np.concatenate([quad + k * nvl for k in range(layers)]).astype(np.uint32)
     rng = np.random.default_rng(seed)
-    count = pos.shape[0] if color_mode == COLOR_VERTEX else idx.shape[0]
+    count = pos.shape[0] if color_mode in (COLOR_VERTEX, COLOR_LIT) else idx.shape[0]
     col = np.empty((count, 4), np.float32)
     col[:, :3] = rng.random((count, 3))
     col[:, 3] = rng.uniform(alpha_range[0], alpha_range[1], count)
+    light = None
+    if color_mode == COLOR_LIT:
+        lit = np.zeros((count, 8), np.float32)
+        lit[:, :4] = col
+        lit[:, 4:7] = np.concatenate(normals)
+        col = lit
+        light = (0.4, 0.6, 1.0, 0.25)
     return Scene(pos, idx, col, color_mode, m, float(n), float(f), width, height,
-                 name=f"layers{layers}x{nx}x{ny}")
+                 name=f"layers{layers}x{nx}x{ny}", light=light)
 
 
 def gaussian_particles(num_quads: int = 2_000_000, width: int = 1920, height: int = 1080,

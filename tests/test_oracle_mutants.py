@@ -5,6 +5,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_pins as pins
+from tests import test_oracle_lit as lpins
 from tests import test_oracle_msaa as mpins
 from tests import test_oracle_threshold as tpins
 
@@ -52,6 +53,13 @@ MUTANTS = {
     "sample_position_ignored": ("int64_t Px = 256 * (int64_t)px + s->sample_x, Py = 256 * (int64_t)py + s->sample_y;",
                                 "int64_t Px = 256 * (int64_t)px + 128, Py = 256 * (int64_t)py + 128;",
                                 [mpins.test_partial_coverage_closed_form]),
+    # lighting: one-sided Lambert (back faces dark)
+    "lit_one_sided": ("fabs(n[0] * L[0] + n[1] * L[1] + n[2] * L[2])", "(n[0] * L[0] + n[1] * L[1] + n[2] * L[2])",
+                      [lpins.test_lighting_invariances]),
+    # lighting: normals interpolated without the perspective weights
+    "lit_affine_normal": ("for (int c = 0; c < 3; ++c) n[c] += wk * (double)ck[4 + c];",
+                          "for (int c = 0; c < 3; ++c) n[c] += l[k] * (double)ck[4 + c];",
+                          [lpins.test_normal_interpolation_on_a_tilted_quad]),
     # near plane ignored
     "no_near_cull": ("} else if (!(w >= s->near_z && w <= s->far_z)) {",
                      "} else if (!(w <= s->far_z)) {",
@@ -67,6 +75,8 @@ def _call(test):
         test(0.5, 7)
     elif test is mpins.test_partial_coverage_closed_form:
         test(4)
+    elif test is lpins.test_lighting_invariances:
+        test("negate_normals")
     else:
         test()
 
