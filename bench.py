@@ -578,6 +578,34 @@ def run_gpu(args):
                 "vs_single_sample_ms": round(m_ms / ms_step, 3)}
         rm.close()
 
+    # ---- lit colours (per-vertex normals, one directional light) on the same layers ------
+    lit = None
+    if world == 1 and args.workload == "layers":
+        lscene = scenegen.wavy_layers(color_mode=scenegen.COLOR_LIT)
+        lds = P.DeviceScene.from_scene(lscene, device=dev)
+        rl = P.Renderer(sorter_k=args.k, carry_colors=carry)
+        rl.set_lighting(lscene.light[:3], lscene.light[3])
+        ol = rl.make_outputs(W, H)
+        vl = rl.view_struct(lds, W, H, ol)
+        rl.render_views([vl])
+        for _ in range(args.warmup):
+            rl.render_views([vl], check=False)
+        l_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(20)]
+        torch.cuda.synchronize()
+        for i, (a0, a1) in enumerate(l_ev):
+            flush.fill_(i & 0xFF)
+            a0.record(stream)
+            rl.render_views([vl], check=False)
+            a1.record(stream)
+        torch.cuda.synchronize()
+        l_ms = sum(a0.elapsed_time(a1) for a0, a1 in l_ev) / len(l_ev)
+        lit = {"ms_per_frame": round(l_ms, 4), "gfrag_s": round(frags / (l_ms * 1e-3) / 1e9, 2),
+               "vs_unlit_ms": round(l_ms / ms_step, 3),
+               "shading": "per fragment: perspective-correct normal, two-sided Lambert + ambient"}
+        rl.close()
+        del lds
+
     # ---- CPU oracle on a bounded sample: full frames for ~10 s ---------------------------
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -626,6 +654,7 @@ def run_gpu(args):
         "overflow_pixel_fraction": overflow_frac,
         "alpha_threshold": alpha_threshold,
         "msaa": msaa,
+        "lit": lit,
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 3), "unit": "Gfrag/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4),

@@ -50,7 +50,10 @@ typedef enum {
                                 match this scene and context (gradients not valid) */
 } lr_status;
 
-enum { LR_COLOR_FLAT = 0, LR_COLOR_VERTEX = 1 };
+/* Colour modes of lr_quads.colors. LR_COLOR_LIT: per-vertex colours with normals and one
+ * directional light (lr_set_lighting); the paper shades its samples with a simple material
+ * (Sec. 2, "Stage 3"; Sec. 4), and this is the plainest shading with normals. */
+enum { LR_COLOR_FLAT = 0, LR_COLOR_VERTEX = 1, LR_COLOR_LIT = 2 };
 
 /* lr_config.flags */
 enum {
@@ -98,7 +101,12 @@ typedef struct {
                                 vertices 4q..4q+3 (then V >= 4Q) */
   int64_t num_quads;         /* Q */
   const float* colors;       /* device, straight RGBA: f32[Q][4] (LR_COLOR_FLAT) or
-                                f32[V][4] (LR_COLOR_VERTEX, interpolated perspective-correctly) */
+                                f32[V][4] (LR_COLOR_VERTEX, interpolated perspective-correctly)
+                                or f32[V][8] (LR_COLOR_LIT: RGBA, normal xyz, one unused
+                                float; colour and normal interpolated perspective-correctly,
+                                RGB then scaled by amb + (1 - amb) |n.L| / |n|, a two-sided
+                                Lambert term plus ambient, alpha unchanged; not with
+                                cov_hash or LR_FLAG_ALPHA_THRESHOLD: LR_ERR_UNSUPPORTED) */
   int32_t color_mode;
   int32_t reserved;
 } lr_quads;
@@ -172,6 +180,13 @@ typedef struct {
 
 /* Create / destroy a context bound to one CUDA device. */
 lr_status lr_create(const lr_config* config, lr_ctx** out_ctx);
+
+/* Light of LR_COLOR_LIT views rendered on this context from now on (also by graphs
+ * created later and by a server started later). light_dir: host float[3], the direction
+ * toward the light in world space (any non-zero length; normalised here); ambient in
+ * [0, 1]. Default: direction (0, 0, 1), ambient 0.25. LR_ERR_INVALID_ARG for a zero or
+ * non-finite direction or an ambient outside [0, 1]. */
+lr_status lr_set_lighting(lr_ctx* ctx, const float* light_dir, float ambient);
 lr_status lr_destroy(lr_ctx* ctx);
 
 /* Bytes of workspace lr_render needs for a scene of num_quads quads at width x height

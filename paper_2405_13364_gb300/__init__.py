@@ -16,10 +16,11 @@ import dataclasses
 import torch
 
 from . import _binding as B
-from ._binding import (LR_COLOR_FLAT, LR_COLOR_VERTEX, LR_ERR_OVERFLOW, LR_FLAG_TIMING, LR_OK,
+from ._binding import (LR_COLOR_FLAT, LR_COLOR_LIT, LR_COLOR_VERTEX, LR_ERR_OVERFLOW, LR_FLAG_TIMING, LR_OK,
                        LrError, lr_camera, lr_config, lr_quads, lr_stats, lr_target, lr_view)
 
 __all__ = ["Renderer", "DeviceScene", "HostStream", "Server", "LrError", "LR_COLOR_FLAT", "LR_COLOR_VERTEX",
+           "LR_COLOR_LIT",
            "composite", "load_library"]
 
 
@@ -38,7 +39,7 @@ class DeviceScene:
 
     positions: torch.Tensor            # f32[V][3]
     indices: torch.Tensor | None       # i32/u32[Q][4] or None
-    colors: torch.Tensor               # f32[Q][4] or f32[V][4]
+    colors: torch.Tensor               # f32[Q][4], f32[V][4], or f32[V][8] (lit: RGBA, normal, unused)
     color_mode: int
     view_proj: tuple                   # 16 floats, row-major
     near: float
@@ -64,7 +65,7 @@ class DeviceScene:
             if idx_t.dtype != torch.int32:
                 idx_t = idx_t.to(torch.int64).to(torch.int32)
             idx = idx_t.to(device).contiguous().reshape(-1, 4)
-        col = dev(colors, torch.float32).reshape(-1, 4)
+        col = dev(colors, torch.float32).reshape(-1, 8 if int(color_mode) == B.LR_COLOR_LIT else 4)
         vp = tuple(float(x) for x in torch.as_tensor(view_proj, dtype=torch.float32).reshape(-1).tolist())
         return cls(pos, idx, col, int(color_mode), vp, float(near), float(far))
 
@@ -113,6 +114,11 @@ class Renderer:
         self.sorter_k = sorter_k
         self._ws = None
         self._ws_bytes = 0
+
+    def set_lighting(self, light_dir, ambient: float):
+        """Light of lit scenes (LR_COLOR_LIT) rendered from now on: direction toward the
+        light in world space (any length) and the ambient term in [0, 1]."""
+        B.lr_set_lighting(self.ctx, light_dir, ambient)
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -325,7 +331,8 @@ class HostStream:
         self.pos = [torch.empty((num_vertices, 3), dtype=torch.float32, device=self.dev) for _ in range(depth)]
         self.idx = [torch.empty((num_quads, 4), dtype=torch.int32, device=self.dev) if indexed else None
                     for _ in range(depth)]
-        self.col = [torch.empty((num_colors, 4), dtype=torch.float32, device=self.dev) for _ in range(depth)]
+        cw = 8 if color_mode == B.LR_COLOR_LIT else 4
+        self.col = [torch.empty((num_colors, cw), dtype=torch.float32, device=self.dev) for _ in range(depth)]
         self.out = [renderer.make_outputs(width, height) for _ in range(depth)]
         self.s_in = torch.cuda.Stream(self.dev)
         self.s_render = torch.cuda.Stream(self.dev)

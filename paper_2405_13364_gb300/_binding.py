@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "LR_OK", 1: "LR_PENDING", -1: "LR_ERR_INVALID_ARG", -2: "LR_E
 
 LR_COLOR_FLAT = 0
 LR_COLOR_VERTEX = 1
+LR_COLOR_LIT = 2
 LR_FLAG_TIMING = 1
 LR_FLAG_CARRY_COLORS = 2
 LR_FLAG_NO_PDL = 4
@@ -110,6 +111,7 @@ _P = ctypes.c_void_p
 _SIGNATURES = {
     "lr_create": (ctypes.c_int, [ctypes.POINTER(lr_config), ctypes.POINTER(_P)]),
     "lr_destroy": (ctypes.c_int, [_P]),
+    "lr_set_lighting": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_float]),
     "lr_workspace_size": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_size_t)]),
     "lr_workspace_size_batch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(lr_view),
@@ -227,6 +229,11 @@ def lr_render_batch(ctx, views, workspace: int, workspace_bytes: int, stream: in
     arr = (lr_view * len(views))(*views)
     _check(ctx, load().lr_render_batch(ctx, len(views), arr, workspace, workspace_bytes, stream),
            "lr_render_batch")
+
+
+def lr_set_lighting(ctx, light_dir, ambient: float):
+    d = (ctypes.c_float * 3)(*[float(v) for v in light_dir])
+    _check(ctx, load().lr_set_lighting(ctx, d, float(ambient)), "lr_set_lighting")
 
 
 def lr_workspace_size_msaa(ctx, num_quads: int, width: int, height: int, n_samples: int) -> int:

@@ -15,6 +15,7 @@
 // data-dependent sizes are read on the device, so the sequence has no host round trip
 // and can be captured into a CUDA graph.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -35,8 +36,8 @@ __global__ void k_bin_sort_big(Ws ws);
 cudaError_t overflow_occupancy(int* blocks_per_sm);
 cudaError_t launch_overflow(bool bwd, const Ws& ws, int grid, cudaStream_t st, bool pdl);
 
-#define LR_DECLARE_RASTER(KK)                                                       \
-  cudaError_t prepare_raster_##KK(int* blocks_flat, int* blocks_vtx, int* blocks_bwd); \
+#define LR_DECLARE_RASTER(KK)                                                                     \
+  cudaError_t prepare_raster_##KK(int* blocks_flat, int* blocks_vtx, int* blocks_bwd, int* blocks_lit); \
   cudaError_t launch_raster_##KK(int mode, const Ws& ws, int grid, cudaStream_t st);
 LR_DECLARE_RASTER(1)
 LR_DECLARE_RASTER(2)
@@ -52,7 +53,7 @@ __global__ void k_write_views(ViewChunk chunk, ViewDev* dst) {
   if (i < chunk.count) dst[chunk.first + i] = chunk.v[i];
 }
 
-typedef cudaError_t (*PrepareFn)(int*, int*, int*);
+typedef cudaError_t (*PrepareFn)(int*, int*, int*, int*);
 typedef cudaError_t (*LaunchFn)(int, const Ws&, int, cudaStream_t);   // mode 0 flat, 1 colours, 2 backward
 
 struct RasterVariant {
@@ -171,7 +172,8 @@ struct lr_ctx {
   int sms = 0;
   lr_config cfg;
   const RasterVariant* variant = nullptr;
-  int raster_blocks_flat = 1, raster_blocks_vtx = 1, raster_blocks_bwd = 1;
+  int raster_blocks_flat = 1, raster_blocks_vtx = 1, raster_blocks_bwd = 1, raster_blocks_lit = 1;
+  float light[4] = {0.f, 0.f, 1.f, 0.25f};   // LR_COLOR_LIT: unit direction toward the light, ambient
   int ovf_blocks = 1;
   // last render, for lr_get_stats
   cudaStream_t last_stream = nullptr;
@@ -229,7 +231,9 @@ extern "C" lr_status lr_create(const lr_config* config, lr_ctx** out_ctx) {
   }
   e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
-  if (e == cudaSuccess) e = c->variant->prepare(&c->raster_blocks_flat, &c->raster_blocks_vtx, &c->raster_blocks_bwd);
+  if (e == cudaSuccess)
+    e = c->variant->prepare(&c->raster_blocks_flat, &c->raster_blocks_vtx, &c->raster_blocks_bwd,
+                            &c->raster_blocks_lit);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bin_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)kSortSmemBytes);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bin_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -246,7 +250,9 @@ extern "C" lr_status lr_create(const lr_config* config, lr_ctx** out_ctx) {
     c->raster_blocks_flat = std::min(c->raster_blocks_flat, g.raster_ctas_per_sm);
     c->raster_blocks_vtx = std::min(c->raster_blocks_vtx, g.raster_ctas_per_sm);
     c->raster_blocks_bwd = std::min(c->raster_blocks_bwd, g.raster_ctas_per_sm);
+    c->raster_blocks_lit = std::min(c->raster_blocks_lit, g.raster_ctas_per_sm);
   }
+  c->raster_blocks_lit = std::max(c->raster_blocks_lit, 1);
   c->raster_blocks_bwd = std::max(c->raster_blocks_bwd, 1);
   c->raster_blocks_flat = std::max(c->raster_blocks_flat, 1);
   c->raster_blocks_vtx = std::max(c->raster_blocks_vtx, 1);
@@ -254,6 +260,21 @@ extern "C" lr_status lr_create(const lr_config* config, lr_ctx** out_ctx) {
   *out_ctx = c;
   return LR_OK;
 }
+
+extern "C" lr_status lr_set_lighting(lr_ctx* ctx, const float* light_dir, float ambient) {
+  if (!ctx || !light_dir) return LR_ERR_INVALID_ARG;
+  const double x = light_dir[0], y = light_dir[1], z = light_dir[2];
+  const double n = std::sqrt(x * x + y * y + z * z);
+  if (!(n > 0.0) || !std::isfinite(n)) return fail(ctx, LR_ERR_INVALID_ARG, "light direction must be finite and non-zero%s");
+  if (!(ambient >= 0.0f && ambient <= 1.0f)) return fail(ctx, LR_ERR_INVALID_ARG, "ambient must lie in [0, 1]%s");
+  ctx->light[0] = (float)(x / n);
+  ctx->light[1] = (float)(y / n);
+  ctx->light[2] = (float)(z / n);
+  ctx->light[3] = ambient;
+  return LR_OK;
+}
+
+const float* lr_internal_light(const lr_ctx* ctx) { return ctx->light; }
 
 extern "C" lr_status lr_destroy(lr_ctx* ctx) {
   if (!ctx) return LR_ERR_INVALID_ARG;
@@ -278,7 +299,7 @@ static lr_status check_view(lr_ctx* c, const lr_view& v) {
     if (!q.positions || !q.colors) return fail(c, LR_ERR_INVALID_ARG, "null positions or colors%s");
     if (!aligned(q.positions, 16) || !aligned(q.colors, 16) || (q.indices && !aligned(q.indices, 16)))
       return fail(c, LR_ERR_INVALID_ARG, "positions, colors and indices must be 16-byte aligned%s");
-    if (q.color_mode != LR_COLOR_FLAT && q.color_mode != LR_COLOR_VERTEX)
+    if (q.color_mode != LR_COLOR_FLAT && q.color_mode != LR_COLOR_VERTEX && q.color_mode != LR_COLOR_LIT)
       return fail(c, LR_ERR_INVALID_ARG, "unknown color_mode%s");
   }
   if (!v.target.rgba || !aligned(v.target.rgba, 16)) return fail(c, LR_ERR_INVALID_ARG, "rgba output must be non-null and 16-byte aligned%s");
@@ -372,17 +393,19 @@ struct Prepared {
   std::vector<ViewDev> vd;
   bool any_vertex = false;
   bool any_hash = false;   // a view asks for the coverage hash (selects the hashing rasteriser)
+  bool any_lit = false;    // a view has lit colours (selects the shading rasteriser)
   Ws ws;
   ViewDev* views_dev = nullptr;
 };
 
 static void describe_views(int32_t n_views, const lr_view* views, std::vector<ViewDev>& vd, bool* any_vertex,
-                           bool* any_hash) {
+                           bool* any_hash, bool* any_lit, const float* light) {
   vd.resize(n_views);
   long long qb = 0, pb = 0;
   int bb = 0, cb = 0;
   *any_vertex = false;
   *any_hash = false;
+  *any_lit = false;
   for (int i = 0; i < n_views; ++i) {
     const lr_view& v = views[i];
     ViewDev& d = vd[i];
@@ -401,6 +424,7 @@ static void describe_views(int32_t n_views, const lr_view* views, std::vector<Vi
       d.m[4 + k] = M[4 + k];
       d.m[8 + k] = M[12 + k];
     }
+    for (int k = 0; k < 4; ++k) d.light[k] = light[k];
     d.near_z = v.camera.near_z;
     d.far_z = v.camera.far_z;
     d.half_w = 0.5f * (float)v.width;
@@ -422,6 +446,7 @@ static void describe_views(int32_t n_views, const lr_view* views, std::vector<Vi
     cb += (int)((v.quads.num_quads + kChunkQuads - 1) / kChunkQuads);
     *any_vertex |= (v.quads.color_mode == LR_COLOR_VERTEX && v.quads.num_quads > 0);
     *any_hash |= v.target.cov_hash != nullptr;
+    *any_lit |= (v.quads.color_mode == LR_COLOR_LIT && v.quads.num_quads > 0);
   }
 }
 
@@ -439,7 +464,9 @@ static lr_status prepare(lr_ctx* ctx, int32_t n_views, const lr_view* views, voi
   if (s != LR_OK) return s;
   set_capacity(P->L, workspace_bytes);
   if (P->L.refs_cap < 1024) return fail(ctx, LR_ERR_OOM, "workspace too small (see lr_workspace_size)%s");
-  describe_views(n_views, views, P->vd, &P->any_vertex, &P->any_hash);
+  describe_views(n_views, views, P->vd, &P->any_vertex, &P->any_hash, &P->any_lit, ctx->light);
+  if (P->any_lit && (P->any_hash || (ctx->cfg.flags & LR_FLAG_ALPHA_THRESHOLD)))
+    return fail(ctx, LR_ERR_UNSUPPORTED, "lit colours with coverage hashes or the alpha threshold%s");
   P->ws = make_ws(P->L, workspace, n_views);
   P->views_dev = reinterpret_cast<ViewDev*>(static_cast<char*>(workspace) + P->L.views);
   return LR_OK;
@@ -491,11 +518,13 @@ static lr_status launch_sequence(lr_ctx* ctx, const Prepared& P, cudaStream_t st
   launch_pdl(pdl, k_bin_sort, dim3(L.total_bins), dim3(256), kSortSmemBytes, st, ws);
   launch_pdl(pdl, k_bin_sort_big, dim3(ctx->sms), dim3(kSortBigThreads), kSortBigSmemBytes, st, ws);
   rec(ctx, timed, 5, st);
-  const bool carry = P.any_vertex || (ctx->cfg.flags & LR_FLAG_CARRY_COLORS);
+  const bool carry = P.any_vertex || P.any_lit || (ctx->cfg.flags & LR_FLAG_CARRY_COLORS);
   const bool ath = !bwd && (ctx->cfg.flags & LR_FLAG_ALPHA_THRESHOLD);   // no hash then (prepare)
-  const int mode = bwd ? 2 : ((carry ? 1 : 0) | (P.any_hash ? 4 : 0) | (ath ? 8 : 0));
+  // (lit views: neither hash nor threshold, see prepare)
+  const int mode = bwd ? 2 : (P.any_lit ? 17 : ((carry ? 1 : 0) | (P.any_hash ? 4 : 0) | (ath ? 8 : 0)));
   ws.t_min = ath ? kAlphaTMin : 0.0f;
-  const int rblocks = bwd ? ctx->raster_blocks_bwd : (carry ? ctx->raster_blocks_vtx : ctx->raster_blocks_flat);
+  const int rblocks = bwd ? ctx->raster_blocks_bwd
+                          : (P.any_lit ? ctx->raster_blocks_lit : (carry ? ctx->raster_blocks_vtx : ctx->raster_blocks_flat));
   cudaError_t e = ctx->variant->launch(mode, ws, ctx->sms * rblocks, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "raster launch");
   rec(ctx, timed, 6, st);
@@ -618,8 +647,9 @@ extern "C" lr_status lr_graph_launch(lr_graph* g, const lr_view* views, lr_strea
       if (s != LR_OK) return s;
     }
     std::vector<ViewDev> vd;
-    bool any_vertex = false, any_hash = false;
-    describe_views(n, views, vd, &any_vertex, &any_hash);
+    bool any_vertex = false, any_hash = false, any_lit = false;
+    // replays keep the light the graph was captured with
+    describe_views(n, views, vd, &any_vertex, &any_hash, &any_lit, g->P.vd[0].light);
     memcpy(g->staging[b], vd.data(), sizeof(ViewDev) * (size_t)n);
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -79,6 +79,7 @@ struct ViewDev {
   int sub_x, sub_y;          // multisampling: the view's sample offset from the pixel centre
                              // (1/256 px), subtracted from the snapped vertices, so that the
                              // pixel-centre tests of every later stage test the sample
+  float light[4];            // lit colours: unit direction toward the light, ambient term
 };
 
 // Up to kViewsPerLaunch view descriptors passed by value to a kernel, which writes them to

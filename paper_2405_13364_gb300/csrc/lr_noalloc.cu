@@ -35,7 +35,7 @@ __global__ void k_bin_scan(Ws ws);
 __global__ void k_bin_scatter(Ws ws);
 __global__ void k_bin_sort(Ws ws);
 __global__ void k_bin_sort_big(Ws ws);
-cudaError_t prepare_raster_3(int* blocks_flat, int* blocks_vtx, int* blocks_bwd);
+cudaError_t prepare_raster_3(int* blocks_flat, int* blocks_vtx, int* blocks_bwd, int* blocks_lit);
 cudaError_t launch_raster_3(int mode, const Ws& ws, int grid, cudaStream_t st);
 cudaError_t overflow_occupancy(int* blocks_per_sm);
 cudaError_t launch_overflow(bool bwd, const Ws& ws, int grid, cudaStream_t st, bool pdl);
@@ -126,9 +126,9 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
     if (!d.ready) {
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LR_ERR_CUDA;
-      int blocks_bwd = 1;
+      int blocks_bwd = 1, blocks_lit = 1;
       if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-          prepare_raster_3(&d.blocks_flat, &d.blocks_vtx, &blocks_bwd) != cudaSuccess ||
+          prepare_raster_3(&d.blocks_flat, &d.blocks_vtx, &blocks_bwd, &blocks_lit) != cudaSuccess ||
           overflow_occupancy(&d.ovf_blocks) != cudaSuccess ||
           cudaFuncSetAttribute(k_bin_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kSortSmemBytes) != cudaSuccess ||

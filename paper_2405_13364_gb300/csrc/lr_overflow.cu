@@ -66,12 +66,30 @@ __device__ __forceinline__ bool frag_eval_r(const Ws& ws, const ViewDev& V, cons
       const uint32_t vb = ib == 1 ? q4.y : (ib == 2 ? q4.z : q4.w);
       const uint32_t vc = ic == 1 ? q4.y : (ic == 2 ? q4.z : q4.w);
       const float wa = __fmul_rn(__ll2float_rn(e[0]), inv) * qa, wb = l1 * qb, wc = l2 * qc;
-      const float4 ca = __ldg(reinterpret_cast<const float4*>(V.col) + va);
-      const float4 cb = __ldg(reinterpret_cast<const float4*>(V.col) + vb);
-      const float4 cc = __ldg(reinterpret_cast<const float4*>(V.col) + vc);
+      // lit views: 32 bytes per vertex, the colour then the normal
+      const bool lit = V.color_mode == LR_COLOR_LIT;
+      const int stride = lit ? 2 : 1;
+      const float4* cv = reinterpret_cast<const float4*>(V.col);
+      const float4 ca = __ldg(cv + (size_t)stride * va);
+      const float4 cb = __ldg(cv + (size_t)stride * vb);
+      const float4 cc = __ldg(cv + (size_t)stride * vc);
       const float r = 1.0f / (wa + wb + wc);
       *col = make_float4((wa * ca.x + wb * cb.x + wc * cc.x) * r, (wa * ca.y + wb * cb.y + wc * cc.y) * r,
                          (wa * ca.z + wb * cb.z + wc * cc.z) * r, (wa * ca.w + wb * cb.w + wc * cc.w) * r);
+      if (lit) {
+        // two-sided Lambert term of the interpolated normal's direction, plus ambient
+        const float4 na = __ldg(cv + 2ull * va + 1), nb = __ldg(cv + 2ull * vb + 1), nc = __ldg(cv + 2ull * vc + 1);
+        const float nx = wa * na.x + wb * nb.x + wc * nc.x;
+        const float ny = wa * na.y + wb * nb.y + wc * nc.y;
+        const float nz = wa * na.z + wb * nb.z + wc * nc.z;
+        const float nn = nx * nx + ny * ny + nz * nz;
+        const float d = fabsf(nx * V.light[0] + ny * V.light[1] + nz * V.light[2]);
+        const float lam = nn > 0.f ? fminf(d * rsqrtf(nn), 1.0f) : 0.f;
+        const float f = V.light[3] + (1.0f - V.light[3]) * lam;
+        col->x *= f;
+        col->y *= f;
+        col->z *= f;
+      }
     }
   }
   return true;

@@ -39,6 +39,9 @@ constexpr uint32_t kTriValid = 1u, kTriFast = 2u, kTriFlatCol = 4u;   // + corr 
 // all three vertices at the same 1/w: the depth key is q0 at every pixel (the
 // interpolation adds l1 * 0 + l2 * 0 with l1, l2 >= 0)
 constexpr uint32_t kTriConstKey = 64u;
+// lit colours (LR_COLOR_LIT): the triangle's colour slots also hold its perspective-weighted
+// normals, and each fragment's RGB is shaded with the view's light
+constexpr uint32_t kTriLit = 128u;
 constexpr unsigned long long kSent = ~0ull;
 constexpr int kRasterThreads = 256;
 #ifndef LR_RASTER_MIN_BLOCKS
@@ -73,10 +76,12 @@ struct __align__(16) TriSm {
 };
 
 // dynamic shared memory of k_raster: per warp 64 triangle records, when fragments carry
-// colours 3 premultiplied vertex colours per triangle, and for the backward 32 gradient
-// slots
-__host__ __device__ constexpr size_t raster_smem_bytes(bool vtx, bool bwd = false) {
-  return (size_t)kRasterWarps * 64 * sizeof(TriSm) + (vtx ? (size_t)kRasterWarps * 64 * 3 * sizeof(float4) : 0) +
+// colours 3 premultiplied vertex colours per triangle (6 slots with lit colours: also the
+// weighted normals), and for the backward 32 gradient slots
+__host__ __device__ constexpr int col_slots(bool lit) { return lit ? 6 : 3; }
+__host__ __device__ constexpr size_t raster_smem_bytes(bool vtx, bool bwd = false, bool lit = false) {
+  return (size_t)kRasterWarps * 64 * sizeof(TriSm) +
+         (vtx ? (size_t)kRasterWarps * 64 * col_slots(lit) * sizeof(float4) : 0) +
          (bwd ? (size_t)kRasterWarps * 32 * sizeof(float4) : 0);
 }
 
@@ -440,16 +445,18 @@ __device__ __forceinline__ void write_pixel(const ViewDev& V, long long pidx, fl
 // HASH: the variant that also writes the per-pixel coverage hash (a test output); the
 // others carry no code or registers for it. ATH: the alpha-threshold variant (forward
 // only, no hash), which also skips candidate quads that cannot reach in front of any
-// pixel of the half-block still blending.
-template <int K, bool VTX, bool BWD, bool HASH, bool ATH = false>
+// pixel of the half-block still blending. LIT: the colour-carrying variant that also
+// shades lit views (per-vertex normals, one directional light).
+template <int K, bool VTX, bool BWD, bool HASH, bool ATH = false, bool LIT = false>
 __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster(Ws ws) {
   pdl_begin();
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int kSlots = col_slots(LIT);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lx = lane & (kHbW - 1), ly = lane >> 3;
   TriSm* tris = reinterpret_cast<TriSm*>(smem) + warp * 64;
-  float4* qcs = reinterpret_cast<float4*>(smem + (size_t)kRasterWarps * 64 * sizeof(TriSm)) + (size_t)warp * 64 * 3;
-  float4* agg = reinterpret_cast<float4*>(smem + raster_smem_bytes(VTX, false)) + (size_t)warp * 32;
+  float4* qcs = reinterpret_cast<float4*>(smem + (size_t)kRasterWarps * 64 * sizeof(TriSm)) + (size_t)warp * 64 * kSlots;
+  float4* agg = reinterpret_cast<float4*>(smem + raster_smem_bytes(VTX, false, LIT)) + (size_t)warp * 32;
   if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
   const unsigned long long nitems = ws.ctrl->raster_items;
   unsigned long long frag_total = 0;
@@ -471,8 +478,11 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
     const bool pix_ok = px < V.width && py < V.height;
     const uint32_t off = ws.bin_off[bin_g];
     const int n = (int)(ws.bin_off[bin_g + 1] - off);
-    const bool vtx_view = V.color_mode == LR_COLOR_VERTEX;
+    const bool vtx_view = V.color_mode != LR_COLOR_FLAT;
     const bool hashing = HASH && V.hash != nullptr;
+    // lit views: unit direction toward the light and the ambient term
+    const float4 light = LIT ? make_float4(V.light[0], V.light[1], V.light[2], V.light[3])
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
 
     PixelState<K, VTX, BWD, ATH> st;
     st.init();
@@ -543,9 +553,41 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
 #pragma unroll
             for (int t = 0; t < 2; ++t)
               if (vsel & (1u << (8 + t))) {
-                qcs[(2 * lane + t) * 3] = fc;
+                qcs[(2 * lane + t) * kSlots] = fc;
                 tris[2 * lane + t].eb.z |= (int)kTriFlatCol;
               }
+          } else if (LIT && V.color_mode == LR_COLOR_LIT) {
+            // 32 bytes per vertex (straight RGBA, then the normal): as below, each triangle
+            // stores its corners' colours times 1/w as (c0, c1 - c0, c2 - c0), then the same
+            // for the normals
+            uint4 vi = make_uint4(4 * jl, 4 * jl + 1, 4 * jl + 2, 4 * jl + 3);
+            if (V.idx) vi = __ldg(reinterpret_cast<const uint4*>(V.idx) + jl);
+            const float4* cv = reinterpret_cast<const float4*>(V.col);
+            const uint32_t vk[4] = {vi.x, vi.y, vi.z, vi.w};
+            float4 p[4], m[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float4 c = __ldg(cv + 2ull * vk[k]), n = __ldg(cv + 2ull * vk[k] + 1);
+              p[k] = make_float4(R.q[k] * c.x, R.q[k] * c.y, R.q[k] * c.z, R.q[k] * c.w);
+              m[k] = make_float4(R.q[k] * n.x, R.q[k] * n.y, R.q[k] * n.z, 0.f);
+            }
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+              if (!(vsel & (1u << (8 + t)))) continue;
+              const uint32_t kb = (vsel >> (4 * t)) & 3u, kc = (vsel >> (4 * t + 2)) & 3u;
+              const float4 a1 = kb == 1 ? p[1] : (kb == 2 ? p[2] : p[3]);
+              const float4 a2 = kc == 1 ? p[1] : (kc == 2 ? p[2] : p[3]);
+              const float4 b1 = kb == 1 ? m[1] : (kb == 2 ? m[2] : m[3]);
+              const float4 b2 = kc == 1 ? m[1] : (kc == 2 ? m[2] : m[3]);
+              float4* qc = qcs + (2 * lane + t) * kSlots;
+              qc[0] = p[0];
+              qc[1] = make_float4(a1.x - p[0].x, a1.y - p[0].y, a1.z - p[0].z, a1.w - p[0].w);
+              qc[2] = make_float4(a2.x - p[0].x, a2.y - p[0].y, a2.z - p[0].z, a2.w - p[0].w);
+              qc[3] = m[0];
+              qc[4] = make_float4(b1.x - m[0].x, b1.y - m[0].y, b1.z - m[0].z, 0.f);
+              qc[5] = make_float4(b2.x - m[0].x, b2.y - m[0].y, b2.z - m[0].z, 0.f);
+              tris[2 * lane + t].eb.z |= (int)kTriLit;
+            }
           } else {
             // the quad's four corner colours times 1/w, loaded together once; each triangle
             // stores (c0, c1 - c0, c2 - c0) of its corners for the fragment's
@@ -564,7 +606,7 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
               const uint32_t kb = (vsel >> (4 * t)) & 3u, kc = (vsel >> (4 * t + 2)) & 3u;
               const float4 a1 = kb == 1 ? p1 : (kb == 2 ? p2 : p3);
               const float4 a2 = kc == 1 ? p1 : (kc == 2 ? p2 : p3);
-              float4* qc = qcs + (2 * lane + t) * 3;
+              float4* qc = qcs + (2 * lane + t) * kSlots;
               qc[0] = p0;
               qc[1] = make_float4(a1.x - p0.x, a1.y - p0.y, a1.z - p0.z, a1.w - p0.w);
               qc[2] = make_float4(a2.x - p0.x, a2.y - p0.y, a2.z - p0.z, a2.w - p0.w);
@@ -597,7 +639,7 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
           const unsigned long long sk = ((unsigned long long)__float_as_uint(key) << 32) | id;
           float4 col = make_float4(0.f, 0.f, 0.f, 0.f);
           if (VTX) {
-            const float4* qc = qcs + (2 * c + t) * 3;
+            const float4* qc = qcs + (2 * c + t) * kSlots;
             if (fl & kTriFlatCol) {
               col = qc[0];
             } else {
@@ -609,6 +651,21 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
               col.y = (a0.y + l1 * d1.y + l2 * d2.y) * rk;
               col.z = (a0.z + l1 * d1.z + l2 * d2.z) * rk;
               col.w = (a0.w + l1 * d1.w + l2 * d2.w) * rk;
+              if (LIT && (fl & kTriLit)) {
+                // the interpolated normal (times the interpolated 1/w, which only scales
+                // it); two-sided Lambert term plus ambient on RGB
+                const float4 m0 = qc[3], e1 = qc[4], e2 = qc[5];
+                const float nx = m0.x + l1 * e1.x + l2 * e2.x;
+                const float ny = m0.y + l1 * e1.y + l2 * e2.y;
+                const float nz = m0.z + l1 * e1.z + l2 * e2.z;
+                const float nn = nx * nx + ny * ny + nz * nz;
+                const float d = fabsf(nx * light.x + ny * light.y + nz * light.z);
+                const float lam = nn > 0.f ? fminf(d * rsqrtf(nn), 1.0f) : 0.f;
+                const float f = light.w + (1.0f - light.w) * lam;
+                col.x *= f;
+                col.y *= f;
+                col.z *= f;
+              }
             }
           }
           st.insert(sk, col, V);
@@ -700,13 +757,14 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
 // parallel.
 #define LR_DEFINE_RASTER(KK)                                                                  \
   namespace lr {                                                                              \
-  template <bool VTX, bool BWD, bool HASH, bool ATH = false>                                  \
+  template <bool VTX, bool BWD, bool HASH, bool ATH = false, bool LIT = false>                \
   static cudaError_t raster_attr_##KK() {                                                     \
-    return cudaFuncSetAttribute(k_raster<KK, VTX, BWD, HASH, ATH>,                            \
+    return cudaFuncSetAttribute(k_raster<KK, VTX, BWD, HASH, ATH, LIT>,                       \
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,                  \
-                                (int)raster_smem_bytes(VTX, BWD));                            \
+                                (int)raster_smem_bytes(VTX, BWD, LIT));                       \
   }                                                                                           \
-  cudaError_t prepare_raster_##KK(int* blocks_flat, int* blocks_vtx, int* blocks_bwd) {       \
+  cudaError_t prepare_raster_##KK(int* blocks_flat, int* blocks_vtx, int* blocks_bwd,         \
+                                  int* blocks_lit) {                                          \
     cudaError_t e = raster_attr_##KK<false, false, false>();                                  \
     if (e == cudaSuccess) e = raster_attr_##KK<true, false, false>();                         \
     if (e == cudaSuccess) e = raster_attr_##KK<false, true, false>();                         \
@@ -714,6 +772,11 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
     if (e == cudaSuccess) e = raster_attr_##KK<true, false, true>();                          \
     if (e == cudaSuccess) e = raster_attr_##KK<false, false, false, true>();                  \
     if (e == cudaSuccess) e = raster_attr_##KK<true, false, false, true>();                   \
+    if (e == cudaSuccess) e = raster_attr_##KK<true, false, false, false, true>();            \
+    if (e != cudaSuccess) return e;                                                           \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                        \
+        blocks_lit, k_raster<KK, true, false, false, false, true>, kRasterThreads,            \
+        raster_smem_bytes(true, false, true));                                                \
     if (e != cudaSuccess) return e;                                                           \
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_flat, k_raster<KK, false, false, false>, \
                                                       kRasterThreads, raster_smem_bytes(false)); \
@@ -725,7 +788,7 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
                                                          kRasterThreads, raster_smem_bytes(true)); \
   }                                                                                           \
   /* mode: 0 flat colours, 1 colours in the sorter, 2 backward; + 4: coverage hash;        \
-     + 8: alpha threshold (modes 8 and 9 only) */                                             \
+     + 8: alpha threshold (modes 8 and 9 only); 17: colours in the sorter with lit views */   \
   cudaError_t launch_raster_##KK(int mode, const Ws& ws, int grid, cudaStream_t st) {         \
     const size_t sf = raster_smem_bytes(false), sv = raster_smem_bytes(true);                 \
     /* a plain launch: with programmatic serialisation the persistent CTAs, placed early  \
@@ -737,6 +800,10 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
       case 5: k_raster<KK, true, false, true><<<grid, kRasterThreads, sv, st>>>(ws); break;   \
       case 8: k_raster<KK, false, false, false, true><<<grid, kRasterThreads, sf, st>>>(ws); break; \
       case 9: k_raster<KK, true, false, false, true><<<grid, kRasterThreads, sv, st>>>(ws); break; \
+      case 17:                                                                                \
+        k_raster<KK, true, false, false, false, true>                                         \
+            <<<grid, kRasterThreads, raster_smem_bytes(true, false, true), st>>>(ws);         \
+        break;                                                                                \
       default: k_raster<KK, false, false, false><<<grid, kRasterThreads, sf, st>>>(ws); break; \
     }                                                                                         \
     return cudaGetLastError();                                                                \

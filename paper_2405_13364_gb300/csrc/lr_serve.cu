@@ -197,6 +197,10 @@ extern "C" lr_status lr_server_start(lr_ctx* ctx, const lr_server_config* config
     delete s;
     return st;
   }
+  {
+    const float* light = lr_internal_light(ctx);   // lit requests use the context's light
+    lr_set_lighting(s->inner, light, light[3]);
+  }
   s->slots.resize(s->cfg.num_slots);
   for (Slot& sl : s->slots) {
     sl.bytes = (size_t)s->cfg.slot_workspace_bytes;

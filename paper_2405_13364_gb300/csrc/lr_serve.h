@@ -10,5 +10,7 @@ struct lr_server;
 lr_server** lr_internal_server_slot(lr_ctx* ctx);
 // the configuration the context was created with (defaults filled in)
 const lr_config* lr_internal_config(const lr_ctx* ctx);
+// the context's light (unit direction toward the light, ambient) for lit views
+const float* lr_internal_light(const lr_ctx* ctx);
 // argument checks of one view, as lr_render_batch applies them (no GPU work)
 lr_status lr_internal_check_view(lr_ctx* ctx, const lr_view* view);
