@@ -6,8 +6,8 @@
  * The pipeline is the paper's sort-middle design (Sec. 2, "Pipeline description"):
  * quad setup (Stage 1), 32x32-pixel binning (Stage 2), per-bin rasterisation with a
  * two-stage sort and blending (Stage 3), plus an exact fallback for pixels whose order
- * the fixed-size sorter cannot guarantee (Sec. 2, "Sample blending": misordered pixels
- * "could be registered and afterwards processed by a slower, conservative algorithm").
+ * the fixed-size sorter cannot guarantee (Sec. 2, "Sample blending", suggests recording
+ * the misordered pixels and redoing them afterwards with a slower exact method).
  *
  * Conventions for every entry point:
  *  - Plain pointers only. Pointers documented as "device" must point to memory of the

@@ -1,7 +1,8 @@
 // lr_overflow.cu -- the exact fallback for pixels whose order the fixed-size per-pixel
 // sorter could not guarantee. The paper detects such pixels by growing the depth filter
-// by one and notes they "could be registered and afterwards processed by a slower,
-// conservative algorithm" (Sec. 2, "Sample blending"; Sec. 3, "Fragment sorting errors").
+// by one and suggests recording them and redoing them afterwards with a slower exact
+// method, which it leaves unbuilt (Sec. 2, "Sample blending"; Sec. 3, "Fragment sorting
+// errors").
 //
 // One warp per registered pixel. The warp takes the candidates of the pixel's half-block
 // from the bin's transposed bitmap (one coalesced load per 1024 references),
