@@ -278,7 +278,8 @@ const char* lr_last_error(const lr_ctx* ctx);
  * is part of the library's device code (every GPU on which that code is loaded holds it
  * until the process exits). It needs no lr_ctx and calls no allocating function (no
  * cudaMalloc / cudaFree / cudaMallocHost, no host heap).
- *  - quads, camera: as for lr_render (device scene, host camera struct).
+ *  - quads, camera: as for lr_render (device scene, host camera struct), with flat or
+ *    per-vertex colours (LR_COLOR_LIT scenes: LR_ERR_INVALID_ARG).
  *  - out_rgba: device f32[H][W][4], 16-byte aligned; written when the stream reaches it.
  *  - device_status: NULL, or a device int32 that receives the GPU-side status of this call
  *    (LR_OK, LR_ERR_OVERFLOW if the scene's bin references did not fit the array,
