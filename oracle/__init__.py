@@ -16,6 +16,8 @@ Functions (each follows the definition stated in ``lr_oracle.c``):
   render_threshold(scene, t)   the opt-in lossy alpha-threshold composite (front to back,
                                a fragment blended only while transmittance > t)
   render64(scene, colors64)    fp64 forward (flat colours) used for finite differences
+Scenes with lit colours (color_mode 2, [V][8] = RGBA, normal, unused) carry their light as
+scene.light = (x, y, z toward the light, ambient).
   backward(scene, grad_out)    fp64 gradient w.r.t. flat per-quad RGBA (Sec. 2 blending,
                                differentiated)
 """
