@@ -5,7 +5,8 @@ rasterisation with the per-pixel sorter, exact overflow path) of the 1080p workl
 32 wavy layers x 256x128 quads = 1,048,576 indexed quads, per-vertex RGBA, mean depth
 complexity 24 (about 49.9M fragments per frame). Inputs are resident in HBM; the L2 is
 flushed (a 512 MiB write) before every timed step and the flush is outside the timed
-events. Prints one JSON line.
+events. Prints one JSON line, which also carries the 1920x1080 particle frame (2M
+flat-colour squares, depth complexity above 1,000) as the `particles` sub-object.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -34,7 +35,6 @@ WORKLOAD = "layers-1080p: 1920x1080, 32 wavy layers x 256x128 = 1,048,576 indexe
 # multiply-adds + 1 compare each) = 9, depth key = 2 int->fp32 conversions + 4 fp32
 # multiplies + 2 adds = 8, sorter = K compare/selects, blend = 8 fp32 ops
 OPS_PER_FRAG_BASE = 25
-SM_COUNT = 152
 # kernels launched per frame (one view): k_init (which also writes the view descriptor),
 # k_setup, k_bin_count, k_bin_scan, k_bin_scatter, k_bin_sort, k_bin_sort_big, k_raster,
 # k_overflow
@@ -163,6 +163,139 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                 "samples": len(self.samples), "period_ms": self.period_ms}
+
+
+def frame_benchmark(P, torch, scene, k, carry, steps, warmup, flush, dev, dist=None):
+    """Device-timed frames of one workload: a renderer without per-stage events renders
+    `steps` frames (L2 flushed before each, outside the events; CUDA events on the stream
+    around each frame), then a second renderer that records an event between stages gives
+    the per-stage breakdown from separate frames. Returns (ms per frame, first-frame stats,
+    stage means, the outputs and view of the timed renderer)."""
+    W, H = scene.width, scene.height
+    ds = P.DeviceScene.from_scene(scene, device=dev)
+    r = P.Renderer(sorter_k=k, carry_colors=carry)
+    rt = P.Renderer(sorter_k=k, timing=True, carry_colors=carry)
+    out = r.make_outputs(W, H)
+    view = r.view_struct(ds, W, H, out)
+    view_t = rt.view_struct(ds, W, H, out)
+    # size the workspace once (retries on reference overflow), then render without checks
+    r.render_views([view])
+    st0 = r.stats()
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(warmup):
+        r.render_views([view], check=False)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev.index or 0)
+    with sampler:
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            r.render_views([view], check=False)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    rt.render_views([view_t])
+    stage_steps = min(steps, 20)
+    stage_sum = {kk: 0.0 for kk in rt.stats()["stage_ms"]}
+    for i in range(stage_steps):
+        flush.fill_(i & 0xFF)
+        rt.render_views([view_t], check=False)
+        st = rt.stats()                 # synchronises; per-stage CUDA events of this frame
+        for kk, v in st["stage_ms"].items():
+            stage_sum[kk] += v
+    rt.close()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    stages = {kk: round(v / stage_steps, 4) for kk, v in stage_sum.items()}
+    return sum(ms) / len(ms), st0, stages, sampler, (r, ds, out, view)
+
+
+def raster_roofline(workload, k, carry, frags, raster_ms, sm_count, sm_max_mhz):
+    """The rasteriser against the plain-ALU peak: algorithmic lane operations per fragment
+    (25 + K) x fragments / its CUDA-event time, against SMs x 128 lanes x the SM clock,
+    with the SM count of the device the run is on; plus the instruction-issue ceiling of
+    the committed ncu capture of the same build, when there is one."""
+    ops = (OPS_PER_FRAG_BASE + k) * frags
+    peak = sm_count * LANES_PER_SM_CLK * sm_max_mhz * 1e6 / 1e12   # T lane-ops/s
+    achieved = ops / (raster_ms * 1e-3) / 1e12
+    traffic, issue_active, inst = raster_capture(workload, k, carry)
+    issue_ceiling = None
+    if inst:
+        ceil_gfrag = sm_count * 4 * sm_max_mhz * 1e6 / (inst / frags) / 1e9
+        got = frags / (raster_ms * 1e-3) / 1e9
+        issue_ceiling = {"warp_instructions_per_fragment": round(inst / frags, 3),
+                         "ceiling_gfrag_s": round(ceil_gfrag, 1), "achieved_gfrag_s": round(got, 1),
+                         "frac": round(got / ceil_gfrag, 4)}
+    return {"bound": "alu", "kernel": "k_raster", "achieved": round(achieved, 4), "peak": round(peak, 3),
+            "unit": "Tlane-op/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+            "ncu_issue_active": issue_active, "ops_per_fragment": OPS_PER_FRAG_BASE + k,
+            "raster_ms": raster_ms,
+            "peak_basis": f"{sm_count} SMs x 128 lanes x {sm_max_mhz:.0f} MHz (max SM clock)",
+            "issue_ceiling": issue_ceiling}
+
+
+def particles_benchmark(P, torch, args, flush, dev, sm_count, hbm_gbs):
+    """The 1920x1080 particle frame (2,000,000 flat-colour squares, centre depth complexity
+    above 1,000) beside the headline: frame time, Gfrag/s, per-stage times, the rasteriser's
+    roofline and the setup / binning HBM fractions, with the autotuned sorter capacity."""
+    import scenegen
+    from paper_2405_13364_gb300 import autotune
+    scene = scenegen.config_particles_1080p()
+    ds = P.DeviceScene.from_scene(scene, device=dev)
+    tuned = autotune.tune(ds, scene.width, scene.height, ks=(1, 2, 3), ctas_per_sm=(0,), reps=3, device=dev)
+    del ds
+    k, carry = tuned["sorter_k"], bool(tuned.get("carry_colors"))
+    ms, st0, stages, sampler, (r, _, _, _) = frame_benchmark(P, torch, scene, k, carry, min(args.steps, 20),
+                                                             args.warmup, flush, dev)
+    r.close()
+    frags = st0["fragments"]
+    clocks = sampler.summary()
+    return {"workload": WORKLOADS["particles"][0], "frame": f"{scene.width}x{scene.height}",
+            "quads": scene.num_quads, "fragments_per_frame": frags, "ms_per_frame": round(ms, 4),
+            "gfrag_s": round(frags / (ms * 1e-3) / 1e9, 3), "sorter_k": k, "carry_colors": carry,
+            "autotune_ms": {f"k{t['sorter_k']}{'c' if t['carry_colors'] else ''}": round(t["ms"], 4)
+                            for t in tuned["table"]},
+            "stage_ms": stages, "overflow_pixels": st0["overflow_pixels"], "bins_high": st0["bins_high"],
+            "sort_bins": st0["sort_bins"],
+            "roofline": raster_roofline("particles", k, carry, frags, stages["raster"], sm_count,
+                                        clocks.get("sm_max_mhz") or 2070.0),
+            **stage_rooflines(scene, st0, stages, hbm_gbs), "clocks": clocks}
+
+
+def stage_rooflines(scene, st0, stages, hbm_gbs):
+    """Setup and binning against the HBM copy bandwidth, two ways: by the algorithmic bytes
+    of the method (indices 16 B per quad, positions 12 B per vertex, a 52-byte record per
+    visible quad (snapped XY 32 B, 1/w 16 B, bin rectangle 4 B) and a 4-byte id per quad for
+    setup; for binning 4 B per visible quad read by each of the two passes, 4 B per
+    reference written, 8 B per bin), and by the bytes this implementation's kernels move
+    (16 B indices + 12 B per vertex + 80 B of records per quad for setup; 12 B read by the
+    count and 16 B by the scatter per quad, 8 B per reference, 16 B per bin for binning)."""
+    W, H = scene.width, scene.height
+    nq, nv = scene.num_quads, scene.num_vertices
+    vis = int(st0["quads_visible"])
+    refs = int(st0["bin_refs"])
+    bins = ((W + 31) // 32) * ((H + 31) // 32)
+    idx = 16 * nq if scene.indices is not None else 0
+    setup_alg = idx + 12 * nv + 52 * vis + 4 * nq
+    setup_impl = idx + 12 * nv + 80 * nq
+    bin_alg = 2 * 4 * vis + 4 * refs + 8 * bins
+    bin_impl = 28 * nq + 8 * refs + 16 * bins
+    out = {}
+    for name, ms, alg, impl in (("setup_hbm", stages.get("setup"), setup_alg, setup_impl),
+                                ("binning_hbm", (stages.get("count") or 0) + (stages.get("scan") or 0)
+                                 + (stages.get("scatter") or 0), bin_alg, bin_impl)):
+        if not ms or not hbm_gbs:
+            out[name] = None
+            continue
+        a = alg / (ms * 1e-3) / 1e9
+        b = impl / (ms * 1e-3) / 1e9
+        out[name] = {"ms": round(ms, 4), "algorithmic_bytes": alg, "achieved_gbs": round(a, 1),
+                     "frac": round(a / hbm_gbs, 4), "implementation_bytes": impl,
+                     "implementation_gbs": round(b, 1), "implementation_frac": round(b / hbm_gbs, 4),
+                     "peak_gbs": hbm_gbs, "peak_basis": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    return out
 
 
 def serving_benchmark(P, torch, num_requests=256, rate_hz=200.0, seed=0):
@@ -376,51 +509,13 @@ def run_gpu(args):
         tuned = autotune.tune(ds, W, H, ks=(1, 2, 3, 4), ctas_per_sm=(0,), reps=3, device=dev)
         args.k = tuned["sorter_k"]
     carry = bool(tuned and tuned.get("carry_colors"))
-    # the timed frames run without per-stage events (the production configuration); the
-    # stage breakdown comes from separate frames of a second renderer that records them
-    r = P.Renderer(sorter_k=args.k, carry_colors=carry)
-    rt = P.Renderer(sorter_k=args.k, timing=True, carry_colors=carry)
-    out = r.make_outputs(W, H)
-    view = r.view_struct(ds, W, H, out)
-    view_t = rt.view_struct(ds, W, H, out)
-    # size the workspace once (retries on reference overflow), then render without checks
-    r.render_views([view])
-    st0 = r.stats()
-    frags = st0["fragments"]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-
-    for _ in range(args.warmup):
-        r.render_views([view], check=False)
-    torch.cuda.synchronize()
-
-    # ---- device-timed steps: L2 flush (untimed), then one frame between two events ----
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    with sampler:
-        for i in range(args.steps):
-            flush.fill_(i & 0xFF)
-            ev[i][0].record(stream)
-            r.render_views([view], check=False)
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
-    # ---- per-stage breakdown: separate frames with a CUDA event between stages ----------
-    rt.render_views([view_t])
-    stage_steps = min(args.steps, 20)
-    stage_sum = {k: 0.0 for k in rt.stats()["stage_ms"]}
-    for i in range(stage_steps):
-        flush.fill_(i & 0xFF)
-        rt.render_views([view_t], check=False)
-        st = rt.stats()                 # synchronises; per-stage CUDA events of this frame
-        for k, v in st["stage_ms"].items():
-            stage_sum[k] += v
+    ms_frame, st0, stages, sampler, (r, ds, out, view) = frame_benchmark(
+        P, torch, scene, args.k, carry, args.steps, args.warmup, flush, dev, dist)
+    frags = st0["fragments"]
     from paper_2405_13364_gb300 import replicas
-    ms = [a.elapsed_time(b) for a, b in ev]
-    ms_step = replicas.max_over_ranks(sum(ms) / len(ms), dist, dev)
+    ms_step = replicas.max_over_ranks(ms_frame, dist, dev)
     if dist:
         dist.barrier()
     value = world * frags / (ms_step * 1e-3) / 1e9
@@ -495,24 +590,15 @@ def run_gpu(args):
         serving = serving_benchmark(P, torch)
         differentiable = differentiable_benchmark(P, torch, steps=20)
 
-    stages = {k: round(v / stage_steps, 4) for k, v in stage_sum.items()}
-    raster_ms = stages["raster"]
-    ops = (OPS_PER_FRAG_BASE + args.k) * frags
     clocks = sampler.summary()
-    sm_max = clocks.get("sm_max_mhz") or 2070.0
-    peak = SM_COUNT * LANES_PER_SM_CLK * sm_max * 1e6 / 1e12   # T lane-ops/s
-    achieved = ops / (raster_ms * 1e-3) / 1e12
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    roofline = raster_roofline(args.workload, args.k, carry, frags, stages["raster"], sm_count,
+                               clocks.get("sm_max_mhz") or 2070.0)
     peaks = _measured_peaks()
-    # the rasteriser's instruction-issue ceiling: every scheduler issuing one warp
-    # instruction per clock, at the captured build's warp instructions per fragment
-    issue_ceiling = None
-    inst = raster_capture(args.workload, args.k, carry)[2]
-    if inst:
-        ceil_gfrag = SM_COUNT * 4 * sm_max * 1e6 / (inst / frags) / 1e9
-        got = frags / (raster_ms * 1e-3) / 1e9
-        issue_ceiling = {"warp_instructions_per_fragment": round(inst / frags, 3),
-                         "ceiling_gfrag_s": round(ceil_gfrag, 1), "achieved_gfrag_s": round(got, 1),
-                         "frac": round(got / ceil_gfrag, 4)}
+    hbm = peaks.get("hbm_gbs") if peaks else None
+    particles = None
+    if args.workload == "layers" and world == 1 and not args.no_particles:
+        particles = particles_benchmark(P, torch, args, flush, dev, sm_count, hbm)
 
     # pixels that needed the exact path, per sorter capacity (the paper's Sec. 3 error rates
     # are for pixels left misordered; here they are recomputed exactly)
@@ -642,15 +728,9 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world} (one frame per GPU per step)"},
         "stage_ms": stages,
         "overflow_pixels": st0["overflow_pixels"],
-        "roofline": {"bound": "alu", "kernel": "k_raster", "achieved": round(achieved, 4),
-                     "peak": round(peak, 3), "unit": "Tlane-op/s", "frac": round(achieved / peak, 4),
-                     "traffic": raster_capture(args.workload, args.k, carry)[0],
-                     "ncu_issue_active": raster_capture(args.workload, args.k, carry)[1],
-                     "ops_per_fragment": OPS_PER_FRAG_BASE + args.k,
-                     "peak_basis": f"{SM_COUNT} SMs x 128 lanes x {sm_max:.0f} MHz (max SM clock)",
-                     "issue_ceiling": issue_ceiling},
-        "setup_hbm": None,
-        "binning_hbm": None,
+        "roofline": roofline,
+        **stage_rooflines(scene, st0, stages, hbm),
+        "particles": particles,
         "overflow_pixel_fraction": overflow_frac,
         "alpha_threshold": alpha_threshold,
         "msaa": msaa,
@@ -667,23 +747,6 @@ def run_gpu(args):
     }
     if peaks:
         line["measured_peaks"] = {"hbm_gbs": peaks.get("hbm_gbs")}
-        # setup is HBM-bound: algorithmic bytes = 16 B indices + 12 B per vertex (each vertex
-        # read once, shared) + 80 B of records written per quad
-        setup_bytes = (16 * scene.num_quads if scene.indices is not None else 0) + 12 * scene.num_vertices + \
-            80 * scene.num_quads
-        if stages.get("setup"):
-            gbs = setup_bytes / (stages["setup"] * 1e-3) / 1e9
-            line["setup_hbm"] = {"achieved_gbs": round(gbs, 1), "peak_gbs": peaks.get("hbm_gbs"),
-                                 "frac": round(gbs / peaks["hbm_gbs"], 4), "bytes": setup_bytes}
-        # binning (count + scan + scatter): 12 B of box and flags read per quad by the count,
-        # 16 B (box, flags, representative depth) by the scatter, 8 B written per reference,
-        # 16 B per bin (count, offset, cursor, order)
-        bin_bytes = 28 * scene.num_quads + 8 * int(st0["bin_refs"]) + 16 * ((W + 31) // 32) * ((H + 31) // 32)
-        bin_ms = stages.get("count", 0) + stages.get("scan", 0) + stages.get("scatter", 0)
-        if bin_ms:
-            gbs = bin_bytes / (bin_ms * 1e-3) / 1e9
-            line["binning_hbm"] = {"achieved_gbs": round(gbs, 1), "peak_gbs": peaks.get("hbm_gbs"),
-                                   "frac": round(gbs / peaks["hbm_gbs"], 4), "bytes": bin_bytes}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -722,6 +785,7 @@ def main():
     ap.add_argument("--k", type=int, default=0, help="sorter capacity K; 0 = autotuned")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-particles", action="store_true", help="skip the particle-frame sub-object")
     ap.add_argument("--profile", action="store_true", help="short run for ncu (see run_profile)")
     ap.add_argument("--workload", default="layers", choices=["layers", "particles", "frustum", "diff"])
     args = ap.parse_args()

@@ -154,6 +154,11 @@ typedef struct {
   int64_t overflow_pixels;   /* pixels re-done by the exact full sort */
   float stage_ms[8];         /* with LR_FLAG_TIMING: setup, count, scan, scatter, sort,
                                 raster, overflow, total */
+  int64_t sort_bins[3];      /* the bins_high bins by how their references were sorted:
+                                [0] bucket sort in shared memory (up to 20480 references,
+                                no bucket over 64), [1] merge sort in shared memory alone
+                                (up to 8192), [2] merge sort of 8192-reference runs merged
+                                through global memory (the rest) */
 } lr_stats;
 
 /* Byte offsets, inside a workspace, of the per-quad records written by the setup stage and
@@ -284,6 +289,10 @@ const char* lr_last_error(const lr_ctx* ctx);
  *  - device_status: NULL, or a device int32 that receives the GPU-side status of this call
  *    (LR_OK, LR_ERR_OVERFLOW if the scene's bin references did not fit the array,
  *    LR_ERR_INVALID_ARG for out-of-range vertex indices); read it after the stream syncs.
+ *    The host-side size check below guarantees room for two references per quad only; a
+ *    scene of larger quads can still need more, and then the GPU reports LR_ERR_OVERFLOW
+ *    and leaves out_rgba unwritten. With device_status NULL nothing reports that case, so
+ *    a caller that cannot rule it out should pass a status word.
  *  - Returns LR_ERR_TOO_LARGE, before any GPU work, when the scene's records plus at least
  *    two bin references per quad do not fit in LR_NOALLOC_SCRATCH_BYTES (roughly: up to
  *    about 480k quads at 1920x1080, or 550k quads at 256x256); LR_ERR_INVALID_ARG for bad

@@ -228,7 +228,7 @@ class Renderer:
                     quads_visible=st.quads_visible, culled=list(st.culled), bin_refs=st.bin_refs,
                     bin_refs_capacity=st.bin_refs_capacity, bins_nonempty=st.bins_nonempty,
                     bins_high=st.bins_high, max_bin_refs=st.max_bin_refs, fragments=st.fragments,
-                    overflow_pixels=st.overflow_pixels,
+                    overflow_pixels=st.overflow_pixels, sort_bins=list(st.sort_bins),
                     stage_ms={n: st.stage_ms[i] for i, n in enumerate(names)})
 
     # ---- differentiation ----------------------------------------------------------------------

@@ -78,7 +78,7 @@ class lr_stats(ctypes.Structure):
                 ("bin_refs_capacity", ctypes.c_int64), ("bins_nonempty", ctypes.c_int64),
                 ("bins_high", ctypes.c_int64), ("max_bin_refs", ctypes.c_int64),
                 ("fragments", ctypes.c_int64), ("overflow_pixels", ctypes.c_int64),
-                ("stage_ms", ctypes.c_float * 8)]
+                ("stage_ms", ctypes.c_float * 8), ("sort_bins", ctypes.c_int64 * 3)]
 
 
 class lr_ws_layout(ctypes.Structure):

@@ -858,6 +858,7 @@ extern "C" lr_status lr_get_stats(lr_ctx* ctx, lr_stats* stats) {
     stats->max_bin_refs = (int64_t)h.max_bin;
     stats->fragments = (int64_t)h.fragments;
     stats->overflow_pixels = (int64_t)h.ovf_count;
+    for (int i = 0; i < 3; ++i) stats->sort_bins[i] = (int64_t)h.sort_branch[i];
     if (ctx->last_timed) {
       for (int i = 0; i < 7; ++i) cudaEventElapsedTime(&stats->stage_ms[i], ctx->ev[i], ctx->ev[i + 1]);
       cudaEventElapsedTime(&stats->stage_ms[7], ctx->ev[0], ctx->ev[7]);

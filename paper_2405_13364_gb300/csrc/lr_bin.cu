@@ -563,11 +563,13 @@ __global__ __launch_bounds__(kSortBigThreads, 1) void k_bin_sort_big(Ws ws) {
     __shared__ uint32_t red[32];
     if (n <= kBucketBigCap &&
         cta_bucket_sort<kBucketsBig>(r, n, sbuf, reinterpret_cast<uint32_t*>(sbuf + kBucketBigCap), red)) {
+      if (threadIdx.x == 0) atomicAdd(&ws.ctrl->sort_branch[0], 1ull);
       write_hb_bitmap(ws, r, n, bin, reinterpret_cast<uint32_t*>(sbuf), (int)(kSortBigSmemBytes / 4));
       __syncthreads();
       continue;
     }
     const int run0 = n <= kSortBigCap ? n : kSortBigCap;
+    if (threadIdx.x == 0) atomicAdd(&ws.ctrl->sort_branch[n <= kSortBigCap ? 1 : 2], 1ull);
     // sort runs of up to kSortBigCap references in shared memory
     for (int s = 0; s < n; s += run0) {
       cta_merge_sort_smem(r + s, min(run0, n - s), sbuf, sbuf + kSortBigCap);

@@ -137,7 +137,10 @@ struct Ctrl {
   unsigned long long bins_high;
   unsigned long long max_bin;
   unsigned long long chunk_list_head;   // allocation cursor of the chunks' (bin, base) lists
-  unsigned long long pad[7];
+  // high-density bins by the sort k_bin_sort_big gave them: bucket sort, merge sort in
+  // shared memory alone, merge sort with runs merged through global memory
+  unsigned long long sort_branch[3];
+  unsigned long long pad[4];
 };
 
 // The per-quad record written by k_setup and gathered by every later stage, 64 bytes so

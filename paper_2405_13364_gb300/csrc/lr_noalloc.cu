@@ -135,6 +135,18 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
           cudaFuncSetAttribute(k_bin_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kSortBigSmemBytes) != cudaSuccess)
         return LR_ERR_CUDA;
+      // Load every kernel this entry point can launch now, not at its first launch: with
+      // CUDA's lazy module loading a kernel's first launch loads it, which a later call
+      // made under stream capture must not do (e.g. a first call without device_status,
+      // then a captured call with one). cudaFuncGetAttributes forces the load.
+      cudaFuncAttributes fa;
+      if (cudaFuncGetAttributes(&fa, k_noalloc_view) != cudaSuccess ||
+          cudaFuncGetAttributes(&fa, k_noalloc_status) != cudaSuccess ||
+          cudaFuncGetAttributes(&fa, k_init) != cudaSuccess || cudaFuncGetAttributes(&fa, k_setup) != cudaSuccess ||
+          cudaFuncGetAttributes(&fa, k_bin_count) != cudaSuccess ||
+          cudaFuncGetAttributes(&fa, k_bin_scan) != cudaSuccess ||
+          cudaFuncGetAttributes(&fa, k_bin_scatter) != cudaSuccess)
+        return LR_ERR_CUDA;
       d.scratch = static_cast<unsigned char*>(p);
       d.blocks_flat = d.blocks_flat > 0 ? d.blocks_flat : 1;
       d.blocks_vtx = d.blocks_vtx > 0 ? d.blocks_vtx : 1;

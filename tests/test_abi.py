@@ -55,6 +55,32 @@ def test_struct_sizes_match_header_layout(lib):
     assert ctypes.sizeof(B.lr_view) == 48 + 72 + 8 + 40
 
 
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    # every binding struct against gcc's layout of the same struct from include/lr.h
+    import subprocess
+    from paper_2405_13364_gb300 import _binding as B
+    names = ["lr_config", "lr_quads", "lr_camera", "lr_target", "lr_view", "lr_stats", "lr_ws_layout",
+             "lr_server_config", "lr_request_info", "lr_server_stats"]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lr.h"', "int main(void) {"]
+    for n in names:
+        lines.append(f'  printf("{n} %zu\\n", sizeof({n}));')
+        for f, _ in getattr(B, n)._fields_:
+            lines.append(f'  printf("{n}.{f} %zu\\n", offsetof({n}, {f}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                  check=True).stdout.splitlines())
+    for n in names:
+        st = getattr(B, n)
+        assert int(out[n]) == ctypes.sizeof(st), n
+        for f, _ in st._fields_:
+            assert int(out[f"{n}.{f}"]) == getattr(st, f).offset, f"{n}.{f}"
+
+
 def test_host_side_argument_errors(lib):
     from paper_2405_13364_gb300 import _binding as B
     assert lib.lr_create(None, None) == B.LR_ERR_INVALID_ARG

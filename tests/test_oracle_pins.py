@@ -192,6 +192,37 @@ def test_brute_force_tiny(k):
     assert r["count"].sum() > 0
 
 
+@pytest.mark.parametrize("k", [0, 6, 7, 8])
+def test_render_pixels_equals_brute_force(k):
+    # the per-pixel entry point (its own gather / sort / composite loop) on every pixel of a
+    # tiny scene, in a shuffled order, against the independent brute force
+    s = _tiny_scenes()[k]
+    rgba, count, hsh = brute.render(s)
+    ys, xs = np.meshgrid(np.arange(s.height), np.arange(s.width), indexing="ij")
+    perm = np.random.default_rng(k).permutation(xs.size)
+    xs, ys = xs.reshape(-1)[perm], ys.reshape(-1)[perm]
+    p = oracle.render_pixels(s, xs, ys)
+    np.testing.assert_array_equal(p["count"], count[ys, xs])
+    np.testing.assert_array_equal(p["hash"], hsh[ys, xs])
+    np.testing.assert_array_equal(p["rgba"], rgba[ys, xs])
+
+
+def test_render_pixels_equals_full_render_on_dense_scenes():
+    # sampled pixels of dense scenes (deep interpenetrating layers, particles), including the
+    # image corners and out-of-order repeats, bit for bit against the full-image render
+    for s in (scenegen.wavy_layers(200, 120, layers=32, nx=40, ny=20, seed=5),
+              scenegen.gaussian_particles(20_000, 160, 90, seed=6)):
+        full = oracle.render(s)
+        rng = np.random.default_rng(1)
+        xs = np.concatenate([rng.integers(0, s.width, 500), [0, s.width - 1, 0, s.width - 1, 7, 7]])
+        ys = np.concatenate([rng.integers(0, s.height, 500), [0, 0, s.height - 1, s.height - 1, 3, 3]])
+        p = oracle.render_pixels(s, xs, ys)
+        np.testing.assert_array_equal(p["count"], full["count"][ys, xs])
+        np.testing.assert_array_equal(p["hash"], full["hash"][ys, xs])
+        np.testing.assert_array_equal(p["rgba"], full["rgba"][ys, xs])
+        assert p["count"].max() > 20
+
+
 def test_depth_key_is_screen_linear_inverse_w():
     s = tilted_plane_quad(64, 64, depth=3.0, slope_x=0.8, slope_y=-0.5, half=1.2)
     st = oracle.setup(s)

@@ -41,14 +41,20 @@ def test_noalloc_matches_lr_render_twice(k):
                 stream.cuda_stream)
     assert B.lr_get_stats(r.ctx).status == 0
     ref_np = ref.cpu().numpy()
-    # the allocation-free entry point, two calls in a row into fresh outputs
-    status = torch.full((1,), 12345, dtype=torch.int32, device="cuda")
+    # the allocation-free entry point, two calls in a row into fresh outputs; the device's
+    # free memory (what cudaMemGetInfo reports) must not move across the second call
+    status = torch.empty((1,), dtype=torch.int32, device="cuda")
     for call in range(2):
         out = torch.full((H, W, 4), float("nan"), dtype=torch.float32, device="cuda")
+        status.fill_(12345)
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         rc = B.lr_render_noalloc(ds.quads_struct(), ds.camera_struct(), W, H, int(out.data_ptr()),
                                  int(status.data_ptr()), stream.cuda_stream)
         assert rc == B.LR_OK, (call, rc)
         torch.cuda.synchronize()
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free_before
         assert int(status.item()) == B.LR_OK
         got = out.cpu().numpy()
         assert np.isfinite(got).all()
@@ -72,3 +78,24 @@ def test_noalloc_rejects_scenes_beyond_its_scratch():
                              None, torch.cuda.current_stream().cuda_stream)
     assert rc == B.LR_ERR_TOO_LARGE
     torch.cuda.synchronize()
+
+
+def test_noalloc_reports_reference_overflow():
+    # 2,000 screen-filling quads at 1920x1080 pass the host-side check (two references per
+    # quad) but need 2,040 references each, far more than the array holds: the GPU status
+    # word says so and the image is left as it was
+    import paper_2405_13364_gb300 as P
+    from paper_2405_13364_gb300 import _binding as B
+    from tests.scene_helpers import rects_scene
+    W, H = 1920, 1080
+    rects = [(0.25, 0.25, W - 0.25, H - 0.25)] * 2000
+    s = rects_scene(rects, width=W, height=H)
+    ds = P.DeviceScene.from_scene(s)
+    out = torch.full((H, W, 4), float("nan"), dtype=torch.float32, device="cuda")
+    status = torch.full((1,), 12345, dtype=torch.int32, device="cuda")
+    rc = B.lr_render_noalloc(ds.quads_struct(), ds.camera_struct(), W, H, int(out.data_ptr()),
+                             int(status.data_ptr()), torch.cuda.current_stream().cuda_stream)
+    assert rc == B.LR_OK
+    torch.cuda.synchronize()
+    assert int(status.item()) == B.LR_ERR_OVERFLOW
+    assert bool(torch.isnan(out).all())
