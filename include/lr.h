@@ -130,12 +130,25 @@ typedef struct {
                                 lr_render_backward can take it to skip its own detection */
 } lr_target;
 
-/* One view of a batch: a scene, a camera, a resolution and its outputs. */
+/* One view of a batch: a scene, a camera, a resolution and its outputs.
+ * owned_tiles: NULL (render the whole frame), or a device bit set over the frame's 32x32-
+ * pixel tiles, u32[ceil(T / 32)] with T = ceil(W / 32) * ceil(H / 32) and tile
+ * (tx, ty) = bit (ty * ceil(W / 32) + tx) % 32 of word (ty * ceil(W / 32) + tx) / 32.
+ * With a set, setup and binning still process every quad of the scene, but only the owned
+ * tiles are depth-sorted and rasterised, and only their pixels of every output (rgba,
+ * rgba8, frag_count, cov_hash, exact_mask) are written; the rest of each output is left
+ * as it was. This is the screen-space split of the sort-middle design (Sec. 2, "Pipeline
+ * description": the screen is cut into bins that are rasterised independently): several
+ * renderers can each take a disjoint tile set of one frame and the tiles are gathered
+ * afterwards. lr_stats.fragments and overflow_pixels then count the owned tiles only.
+ * Not with lr_render_backward's own view, lr_render_msaa or lr_render_noalloc (which take
+ * no lr_view). */
 typedef struct {
   lr_quads quads;
   lr_camera camera;
   int32_t width, height;
   lr_target target;
+  const uint32_t* owned_tiles;
 } lr_view;
 
 typedef struct {

@@ -156,10 +156,19 @@ class Renderer:
         return o
 
     @staticmethod
-    def view_struct(scene: DeviceScene, width: int, height: int, out: Outputs) -> lr_view:
+    def view_struct(scene: DeviceScene, width: int, height: int, out: Outputs,
+                    owned_tiles: torch.Tensor | None = None) -> lr_view:
+        """owned_tiles: None, or a device int32/uint32 tensor holding the bit set of the
+        32x32-pixel tiles to rasterise (partition.owned_bitset's layout); the other tiles'
+        pixels of every output are left as they are."""
         tgt = lr_target(_ptr(out["rgba"]), _ptr(out.get("rgba8")), _ptr(out.get("count")),
                         _ptr(out.get("hash")), _ptr(out.get("exact_mask")))
-        return lr_view(scene.quads_struct(), scene.camera_struct(), width, height, tgt)
+        if owned_tiles is not None:
+            ntiles = ((width + 31) // 32) * ((height + 31) // 32)
+            if owned_tiles.numel() < (ntiles + 31) // 32 or owned_tiles.element_size() != 4 \
+                    or not owned_tiles.is_cuda or not owned_tiles.is_contiguous():
+                raise ValueError("owned_tiles: a contiguous device tensor of ceil(tiles / 32) 32-bit words")
+        return lr_view(scene.quads_struct(), scene.camera_struct(), width, height, tgt, _ptr(owned_tiles))
 
     def render_views(self, views, stream=None, check: bool = True):
         """Render lr_view structs with one lr_render_batch call; grows the workspace and
@@ -181,9 +190,12 @@ class Renderer:
         raise LrError(LR_ERR_OVERFLOW, "bin references kept exceeding the workspace")
 
     def render(self, scene: DeviceScene, width: int, height: int, rgba8=False, count=False,
-               hash=False, stream=None, check: bool = True, exact_mask=False) -> Outputs:
-        out = self.make_outputs(width, height, rgba8, count, hash, exact_mask)
-        self.render_views([self.view_struct(scene, width, height, out)], stream, check)
+               hash=False, stream=None, check: bool = True, exact_mask=False, owned_tiles=None,
+               out: Outputs | None = None) -> Outputs:
+        """owned_tiles: see view_struct. out: outputs to render into (default: new ones)."""
+        if out is None:
+            out = self.make_outputs(width, height, rgba8, count, hash, exact_mask)
+        self.render_views([self.view_struct(scene, width, height, out, owned_tiles)], stream, check)
         return out
 
     def render_msaa(self, scene: DeviceScene, width: int, height: int, samples: int = 4, offsets=None,

@@ -304,7 +304,8 @@ static lr_status check_view(lr_ctx* c, const lr_view& v) {
   }
   if (!v.target.rgba || !aligned(v.target.rgba, 16)) return fail(c, LR_ERR_INVALID_ARG, "rgba output must be non-null and 16-byte aligned%s");
   if ((v.target.rgba8 && !aligned(v.target.rgba8, 4)) || (v.target.frag_count && !aligned(v.target.frag_count, 4)) ||
-      (v.target.cov_hash && !aligned(v.target.cov_hash, 8)) || (v.target.exact_mask && !aligned(v.target.exact_mask, 4)))
+      (v.target.cov_hash && !aligned(v.target.cov_hash, 8)) || (v.target.exact_mask && !aligned(v.target.exact_mask, 4)) ||
+      (v.owned_tiles && !aligned(v.owned_tiles, 4)))
     return fail(c, LR_ERR_INVALID_ARG, "misaligned optional output%s");
   const float n = v.camera.near_z, f = v.camera.far_z;
   if (!(n > 0.0f) || !(f >= n) || !(f < 3.4e38f)) return fail(c, LR_ERR_INVALID_ARG, "need 0 < near <= far < inf%s");
@@ -418,6 +419,7 @@ static void describe_views(int32_t n_views, const lr_view* views, std::vector<Vi
     d.cnt = v.target.frag_count;
     d.hash = reinterpret_cast<unsigned long long*>(v.target.cov_hash);
     d.xmask = v.target.exact_mask;
+    d.owned = v.owned_tiles;
     const float* M = v.camera.view_proj;
     for (int k = 0; k < 4; ++k) {
       d.m[k] = M[k];

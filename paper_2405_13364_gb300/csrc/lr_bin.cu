@@ -526,6 +526,16 @@ __device__ __forceinline__ void cta_merge_sort_smem(unsigned long long* g, int n
   for (int i = t; i < n; i += T) g[i] = src[i];
 }
 
+// Whether a bin (a 32x32-pixel tile) is rasterised by this render (its view's owned-tile
+// set, when it has one).
+__device__ __forceinline__ bool bin_owned(const Ws& ws, int bin) {
+  const int v = view_of_bin(ws.views, ws.n_views, bin);
+  const ViewDev& V = ws.views[v];
+  if (!V.owned) return true;
+  const int b = bin - V.bin_base;
+  return tile_owned(V, (b % V.nbx) << kBinLog2, (b / V.nbx) << kBinLog2);
+}
+
 __global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {
   pdl_begin();
   extern __shared__ unsigned long long sbuf[];
@@ -534,6 +544,7 @@ __global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {
   const uint32_t off = ws.bin_off[bin];
   const int n = (int)(ws.bin_off[bin + 1] - off);
   if (n >= kSortSmemCap) return;   // high-density: k_bin_sort_big
+  if (!bin_owned(ws, bin)) return;  // a tile another renderer rasterises
   unsigned long long* r = ws.refs + off;
   if (n > 1) {
     cta_merge_sort_smem(r, n, sbuf, sbuf + kSortSmemCap);
@@ -557,6 +568,7 @@ __global__ __launch_bounds__(kSortBigThreads, 1) void k_bin_sort_big(Ws ws) {
     const int bin = s_bin;
     __syncthreads();
     if (bin < 0) return;
+    if (!bin_owned(ws, bin)) continue;
     const uint32_t off = ws.bin_off[bin];
     const int n = (int)(ws.bin_off[bin + 1] - off);
     unsigned long long* r = ws.refs + off;

@@ -64,6 +64,7 @@ struct ViewDev {
   uint32_t* cnt;             // optional
   unsigned long long* hash;  // optional
   uint32_t* xmask;           // optional: exact-path bits per 8x4 half-block
+  const uint32_t* owned;     // optional: bit set of the 32x32-pixel tiles to rasterise
   float m[12];               // rows 0, 1, 3 of the view-projection (x, y, w)
   float near_z, far_z;
   float half_w, half_h;
@@ -81,6 +82,14 @@ struct ViewDev {
                              // pixel-centre tests of every later stage test the sample
   float light[4];            // lit colours: unit direction toward the light, ambient term
 };
+
+// Whether the 32x32-pixel tile holding pixel (px, py) is to be rasterised (every tile when
+// the view has no owned-tile set).
+__device__ __forceinline__ bool tile_owned(const ViewDev& V, int px, int py) {
+  if (!V.owned) return true;
+  const int t = (py >> 5) * ((V.width + 31) >> 5) + (px >> 5);
+  return (__ldg(V.owned + (t >> 5)) >> (t & 31)) & 1u;
+}
 
 // Up to kViewsPerLaunch view descriptors passed by value to a kernel, which writes them to
 // the workspace (no host buffer is needed).

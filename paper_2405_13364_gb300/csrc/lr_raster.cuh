@@ -473,7 +473,7 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
     const int b = bin_g - V.bin_base;
     const int bx = b % V.nbx, by = b / V.nbx;
     const int ox = (bx << kBinLog2) + (hb & 3) * kHbW, oy = (by << kBinLog2) + (hb >> 2) * kHbH;
-    if (ox >= V.width || oy >= V.height) continue;
+    if (ox >= V.width || oy >= V.height || !tile_owned(V, ox, oy)) continue;
     const int px = ox + lx, py = oy + ly;
     const bool pix_ok = px < V.width && py < V.height;
     const uint32_t off = ws.bin_off[bin_g];

@@ -2,9 +2,9 @@
 
 Frames, views and served requests are independent, so N GPUs render disjoint shares of
 the work; the only cross-rank operations are for measurement (a barrier and the maximum
-of the per-rank times). The sort-middle design would also allow a screen-space split of
-one frame (each GPU rasterising its own bins after a full setup + binning, then gathering
-tiles), but every box of this deployment has one GPU, so that split is not built.
+of the per-rank times). The screen-space split of one frame over several GPUs (each
+rasterising its own tiles after a full setup and binning, then one gather of the tiles)
+lives in partition.py.
 """
 from __future__ import annotations
 
