@@ -300,38 +300,51 @@ def stage_rooflines(scene, st0, stages, hbm_gbs):
 
 def serving_benchmark(P, torch, num_requests=256, rate_hz=200.0, seed=0):
     """The served render stream: a seeded Poisson trace of mixed requests (resolutions
-    256x256 .. 2560x1440, the three scene generators at 10k-2M quads), served by the
-    continuous-batching server, against the same trace served one lr_render at a time.
-    Scenes are built and uploaded before the clock starts (a pool of 15 geometries: three
-    generators x five log-spaced sizes; each request uses the pooled geometry of its kind
-    nearest to its quad count, with a camera for its resolution). Returns a dict."""
-    import math
+    256x256 .. 2560x1440, the three scene generators at quad counts log-uniform in
+    10k-2M), served by the continuous-batching server, against the same trace served one
+    lr_render at a time. Every request renders with the sorter capacity the autotuner
+    picks for its size bucket (GPU, resolution, quad count and colour mode, each rounded
+    to a power of two), in both forms. Scenes are built and uploaded before the clock
+    starts: layer requests get their own grid scaled to the quad count; particle and
+    frustum requests take the first N quads of one 2M-quad scene per generator and
+    resolution, which has the same distribution as a fresh N-quad scene (quads are drawn
+    independently). Returns a dict."""
     import time as _time
 
     import numpy as np
 
     import scenegen
+    from paper_2405_13364_gb300 import autotune
     trace = scenegen.request_trace(num_requests, rate_hz, seed=seed)
-    sizes = [10_000, 40_000, 160_000, 640_000, 2_000_000]
-    pool = {}
-    for kind in ("frustum", "layers", "particles"):
-        for q in sizes:
-            sc = scenegen.scene_for_request(dict(kind=kind, quads=q, width=1920, height=1080, seed=7))
-            pool[(kind, q)] = P.DeviceScene.from_scene(sc)
+    base = {}
 
     def scene_of(req):
-        q = min(sizes, key=lambda s: abs(math.log(s) - math.log(req["quads"])))
-        base = pool[(req["kind"], q)]
-        m, n, f = scenegen.perspective(req["width"], req["height"])
-        return P.DeviceScene(base.positions, base.indices, base.colors, base.color_mode,
-                             tuple(float(x) for x in m.reshape(-1)), float(n), float(f))
+        kind, q, w, h = req["kind"], req["quads"], req["width"], req["height"]
+        if kind == "layers":
+            return P.DeviceScene.from_scene(scenegen.scene_for_request(req))
+        key = (kind, w, h)
+        if key not in base:
+            big = dict(req, quads=2_000_000, seed=7)
+            base[key] = P.DeviceScene.from_scene(scenegen.scene_for_request(big))
+        b = base[key]
+        return P.DeviceScene(b.positions[: 4 * q], None, b.colors[:q], b.color_mode, b.view_proj, b.near, b.far)
 
     scenes = [scene_of(r) for r in trace]
+    # the autotuned sorter capacity of every request's size bucket (tuned once per bucket,
+    # on the bucket's first request)
+    ks, tuned_buckets = [], {}
+    for sc, q in zip(scenes, trace):
+        key = autotune.workload_key(q["width"], q["height"], sc.num_quads, sc.color_mode)
+        if key not in tuned_buckets:
+            tuned_buckets[key] = autotune.tune(sc, q["width"], q["height"], ks=(1, 2, 3), reps=3,
+                                               carry=(False,))["sorter_k"]
+        ks.append(tuned_buckets[key])
     frags = 0
     # ---- sequential: one lr_render per request, in arrival order, one at a time -----------
     r = P.Renderer(sorter_k=3)
     outs = [r.make_outputs(q["width"], q["height"]) for q in trace]
-    views = [P.Renderer.view_struct(s, q["width"], q["height"], o) for s, q, o in zip(scenes, trace, outs)]
+    views = [P.Renderer.view_struct(s, q["width"], q["height"], o, sorter_k=k)
+             for s, q, o, k in zip(scenes, trace, outs, ks)]
     for v in views[:8]:
         r.render_views([v])                      # warm-up, sizes the workspace
     ref_imgs = []
@@ -355,7 +368,7 @@ def serving_benchmark(P, torch, num_requests=256, rate_hz=200.0, seed=0):
     r.close()
     # ---- served: continuous batching ---------------------------------------------------------
     srv = P.Server(sorter_k=3, num_slots=3, max_batch_views=8, slot_workspace_bytes=2 << 30)
-    warm = [srv.submit(scenes[i], trace[i]["width"], trace[i]["height"]) for i in range(8)]
+    warm = [srv.submit(scenes[i], trace[i]["width"], trace[i]["height"], sorter_k=ks[i]) for i in range(8)]
     for t in warm:
         while srv.poll(t, timeout_us=100_000) is None:
             pass
@@ -370,7 +383,7 @@ def serving_benchmark(P, torch, num_requests=256, rate_hz=200.0, seed=0):
                 now = _time.perf_counter() - tb
                 if now < q["arrival"]:
                     _time.sleep(q["arrival"] - now)
-            tickets.append(srv.submit(scenes[i], q["width"], q["height"], out=souts[i]))
+            tickets.append(srv.submit(scenes[i], q["width"], q["height"], out=souts[i], sorter_k=ks[i]))
         lat, last_done = [], 0
         for i, t in enumerate(tickets):
             res = None
@@ -400,6 +413,10 @@ def serving_benchmark(P, torch, num_requests=256, rate_hz=200.0, seed=0):
         "sequential": {"fps": round(num_requests / seq_span, 1), "p50_ms": round(pct(seq_lat, 50), 3),
                        "p99_ms": round(pct(seq_lat, 99), 3), "saturated_fps": round(num_requests / seq_sat, 1)},
         "served_equals_sequential_bitwise": bool(same),
+        "sorter_k_per_request": {f"k{k}": ks.count(k) for k in sorted(set(ks))},
+        "size_buckets_tuned": len(tuned_buckets),
+        "quads_per_request": {"min": min(s_.num_quads for s_ in scenes), "max": max(s_.num_quads for s_ in scenes),
+                              "total": sum(s_.num_quads for s_ in scenes)},
     }
 
 

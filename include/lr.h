@@ -142,13 +142,20 @@ typedef struct {
  * renderers can each take a disjoint tile set of one frame and the tiles are gathered
  * afterwards. lr_stats.fragments and overflow_pixels then count the owned tiles only.
  * Not with lr_render_backward's own view, lr_render_msaa or lr_render_noalloc (which take
- * no lr_view). */
+ * no lr_view).
+ * sorter_k: 0 (the context's sorter capacity) or the capacity for this view, one of 1, 2,
+ * 3, 4, 6, 8, 12 (any capacity gives the same exact image; it only changes which pixels
+ * take the exact path, and so the speed). All views of one lr_render_batch call must
+ * resolve to the same capacity (LR_ERR_INVALID_ARG otherwise); the server batches only
+ * requests of equal capacity. */
 typedef struct {
   lr_quads quads;
   lr_camera camera;
   int32_t width, height;
   lr_target target;
   const uint32_t* owned_tiles;
+  int32_t sorter_k;
+  int32_t reserved;
 } lr_view;
 
 typedef struct {
@@ -244,8 +251,8 @@ lr_status lr_render_batch(lr_ctx* ctx, int32_t n_views, const lr_view* views, vo
  * lr_graph_create captures the launch sequence of lr_render_batch for these views into a
  * CUDA graph bound to this workspace. lr_graph_launch replays it on a stream; views may
  * be NULL (render the captured views again) or new views with the same shapes (per view:
- * width, height, num_quads, color_mode, whether a coverage hash is written); scene and
- * output pointers and cameras may change.
+ * width, height, num_quads, color_mode, whether a coverage hash is written, sorter
+ * capacity); scene and output pointers, owned-tile sets and cameras may change.
  * Replays read the view descriptors from one of two pinned host buffers owned by the
  * graph; a launch waits (host side) for the replay two launches back. The graph, its
  * workspace and the context must outlive every replay; lr_get_stats reports the last one. */
@@ -363,7 +370,9 @@ typedef struct {
   int32_t num_slots;             /* batches in flight at once; default 2 */
   int32_t max_batch_views;       /* views per batch; default 16 */
   int64_t slot_workspace_bytes;  /* device workspace per slot; default 512 MiB */
-  int32_t poll_interval_us;      /* completion polling period of the server thread; default 20 */
+  int32_t poll_interval_us;      /* while batches run, the server thread polls their completion
+                                    in a spin for up to this long between looks at the queue
+                                    (new requests end the spin early); default 20 */
   int32_t reserved;
 } lr_server_config;
 

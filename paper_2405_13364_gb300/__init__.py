@@ -157,10 +157,11 @@ class Renderer:
 
     @staticmethod
     def view_struct(scene: DeviceScene, width: int, height: int, out: Outputs,
-                    owned_tiles: torch.Tensor | None = None) -> lr_view:
+                    owned_tiles: torch.Tensor | None = None, sorter_k: int = 0) -> lr_view:
         """owned_tiles: None, or a device int32/uint32 tensor holding the bit set of the
         32x32-pixel tiles to rasterise (partition.owned_bitset's layout); the other tiles'
-        pixels of every output are left as they are."""
+        pixels of every output are left as they are. sorter_k: 0 for the renderer's sorter
+        capacity, else this view's (all views of one batch must agree)."""
         tgt = lr_target(_ptr(out["rgba"]), _ptr(out.get("rgba8")), _ptr(out.get("count")),
                         _ptr(out.get("hash")), _ptr(out.get("exact_mask")))
         if owned_tiles is not None:
@@ -168,7 +169,8 @@ class Renderer:
             if owned_tiles.numel() < (ntiles + 31) // 32 or owned_tiles.element_size() != 4 \
                     or not owned_tiles.is_cuda or not owned_tiles.is_contiguous():
                 raise ValueError("owned_tiles: a contiguous device tensor of ceil(tiles / 32) 32-bit words")
-        return lr_view(scene.quads_struct(), scene.camera_struct(), width, height, tgt, _ptr(owned_tiles))
+        return lr_view(scene.quads_struct(), scene.camera_struct(), width, height, tgt, _ptr(owned_tiles),
+                       int(sorter_k), 0)
 
     def render_views(self, views, stream=None, check: bool = True):
         """Render lr_view structs with one lr_render_batch call; grows the workspace and
@@ -443,9 +445,11 @@ class Server:
         self.running = True
 
     def submit(self, scene: DeviceScene, width: int, height: int, out: Outputs | None = None,
-               **outputs) -> int:
+               sorter_k: int = 0, **outputs) -> int:
+        """sorter_k: 0 for the server's capacity, else this request's (e.g. autotuned for its
+        size); the server batches requests of equal capacity only."""
         out = out if out is not None else self.renderer.make_outputs(width, height, **outputs)
-        view = Renderer.view_struct(scene, width, height, out)
+        view = Renderer.view_struct(scene, width, height, out, sorter_k=sorter_k)
         t = B.lr_submit(self.ctx, view)
         self._live[t] = (scene, out)
         return t

@@ -68,7 +68,8 @@ class lr_target(ctypes.Structure):
 
 class lr_view(ctypes.Structure):
     _fields_ = [("quads", lr_quads), ("camera", lr_camera), ("width", ctypes.c_int32),
-                ("height", ctypes.c_int32), ("target", lr_target), ("owned_tiles", ctypes.c_void_p)]
+                ("height", ctypes.c_int32), ("target", lr_target), ("owned_tiles", ctypes.c_void_p),
+                ("sorter_k", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class lr_stats(ctypes.Structure):

@@ -167,12 +167,20 @@ static Ws make_ws(const Layout& L, void* base, int n_views) {
 
 using namespace lr;
 
+// A rasteriser variant (sorter capacity K) with its resident CTAs per SM for each colour
+// layout, the launch grid of its persistent kernels.
+struct VariantState {
+  const RasterVariant* v = nullptr;
+  int flat = 1, vtx = 1, bwd = 1, lit = 1;
+};
+
 struct lr_ctx {
   int device = 0;
   int sms = 0;
   lr_config cfg;
-  const RasterVariant* variant = nullptr;
-  int raster_blocks_flat = 1, raster_blocks_vtx = 1, raster_blocks_bwd = 1, raster_blocks_lit = 1;
+  VariantState vs[sizeof(kVariants) / sizeof(kVariants[0])];
+  int variant = 0;             // index of the context's default sorter capacity in vs
+  int pdl_override = -1;       // -1: as cfg.flags say; 0 / 1: this render without / with PDL
   float light[4] = {0.f, 0.f, 1.f, 0.25f};   // LR_COLOR_LIT: unit direction toward the light, ambient
   int ovf_blocks = 1;
   // last render, for lr_get_stats
@@ -190,6 +198,7 @@ struct lr_ctx {
 };
 
 lr_server** lr_internal_server_slot(lr_ctx* ctx) { return &ctx->server; }
+void lr_internal_set_pdl(lr_ctx* ctx, int pdl) { ctx->pdl_override = pdl; }
 const lr_config* lr_internal_config(const lr_ctx* ctx) { return &ctx->cfg; }
 
 static lr_status fail(lr_ctx* c, lr_status s, const char* fmt, const char* detail = "") {
@@ -218,9 +227,10 @@ extern "C" lr_status lr_create(const lr_config* config, lr_ctx** out_ctx) {
     delete c;
     return LR_ERR_INVALID_ARG;
   }
-  for (const auto& v : kVariants)
-    if (v.k == g.sorter_k) c->variant = &v;
-  if (!c->variant) {
+  c->variant = -1;
+  for (int i = 0; i < (int)(sizeof(kVariants) / sizeof(kVariants[0])); ++i)
+    if (kVariants[i].k == g.sorter_k) c->variant = i;
+  if (c->variant < 0) {
     delete c;
     return LR_ERR_INVALID_ARG;
   }
@@ -231,9 +241,22 @@ extern "C" lr_status lr_create(const lr_config* config, lr_ctx** out_ctx) {
   }
   e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
-  if (e == cudaSuccess)
-    e = c->variant->prepare(&c->raster_blocks_flat, &c->raster_blocks_vtx, &c->raster_blocks_bwd,
-                            &c->raster_blocks_lit);
+  // every sorter capacity is prepared, so that a view may ask for its own (lr_view.sorter_k)
+  for (int i = 0; i < (int)(sizeof(kVariants) / sizeof(kVariants[0])) && e == cudaSuccess; ++i) {
+    VariantState& V = c->vs[i];
+    V.v = &kVariants[i];
+    e = V.v->prepare(&V.flat, &V.vtx, &V.bwd, &V.lit);
+    if (g.raster_ctas_per_sm > 0) {
+      V.flat = std::min(V.flat, g.raster_ctas_per_sm);
+      V.vtx = std::min(V.vtx, g.raster_ctas_per_sm);
+      V.bwd = std::min(V.bwd, g.raster_ctas_per_sm);
+      V.lit = std::min(V.lit, g.raster_ctas_per_sm);
+    }
+    V.flat = std::max(V.flat, 1);
+    V.vtx = std::max(V.vtx, 1);
+    V.bwd = std::max(V.bwd, 1);
+    V.lit = std::max(V.lit, 1);
+  }
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bin_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)kSortSmemBytes);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bin_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -246,16 +269,6 @@ extern "C" lr_status lr_create(const lr_config* config, lr_ctx** out_ctx) {
     lr_destroy(c);
     return s;
   }
-  if (g.raster_ctas_per_sm > 0) {
-    c->raster_blocks_flat = std::min(c->raster_blocks_flat, g.raster_ctas_per_sm);
-    c->raster_blocks_vtx = std::min(c->raster_blocks_vtx, g.raster_ctas_per_sm);
-    c->raster_blocks_bwd = std::min(c->raster_blocks_bwd, g.raster_ctas_per_sm);
-    c->raster_blocks_lit = std::min(c->raster_blocks_lit, g.raster_ctas_per_sm);
-  }
-  c->raster_blocks_lit = std::max(c->raster_blocks_lit, 1);
-  c->raster_blocks_bwd = std::max(c->raster_blocks_bwd, 1);
-  c->raster_blocks_flat = std::max(c->raster_blocks_flat, 1);
-  c->raster_blocks_vtx = std::max(c->raster_blocks_vtx, 1);
   c->ovf_blocks = std::max(c->ovf_blocks, 1);
   *out_ctx = c;
   return LR_OK;
@@ -309,6 +322,11 @@ static lr_status check_view(lr_ctx* c, const lr_view& v) {
     return fail(c, LR_ERR_INVALID_ARG, "misaligned optional output%s");
   const float n = v.camera.near_z, f = v.camera.far_z;
   if (!(n > 0.0f) || !(f >= n) || !(f < 3.4e38f)) return fail(c, LR_ERR_INVALID_ARG, "need 0 < near <= far < inf%s");
+  if (v.sorter_k) {
+    bool known = false;
+    for (const auto& kv : kVariants) known |= kv.k == v.sorter_k;
+    if (!known) return fail(c, LR_ERR_INVALID_ARG, "sorter_k must be 0 or one of 1, 2, 3, 4, 6, 8, 12%s");
+  }
   return LR_OK;
 }
 
@@ -397,6 +415,7 @@ struct Prepared {
   bool any_lit = false;    // a view has lit colours (selects the shading rasteriser)
   Ws ws;
   ViewDev* views_dev = nullptr;
+  int variant = 0;         // the batch's sorter capacity (index into lr_ctx::vs)
 };
 
 static void describe_views(int32_t n_views, const lr_view* views, std::vector<ViewDev>& vd, bool* any_vertex,
@@ -462,6 +481,17 @@ static lr_status prepare(lr_ctx* ctx, int32_t n_views, const lr_view* views, voi
     if ((ctx->cfg.flags & LR_FLAG_ALPHA_THRESHOLD) && (views[i].target.frag_count || views[i].target.cov_hash))
       return fail(ctx, LR_ERR_UNSUPPORTED, "fragment counts and coverage hashes need the exact composite%s");
   }
+  // the batch's sorter capacity: every view's own (lr_view.sorter_k) or the context's
+  P->variant = ctx->variant;
+  for (int i = 0; i < n_views; ++i) {
+    const int k = views[i].sorter_k ? views[i].sorter_k : ctx->cfg.sorter_k;
+    int vi = -1;
+    for (int j = 0; j < (int)(sizeof(kVariants) / sizeof(kVariants[0])); ++j)
+      if (kVariants[j].k == k) vi = j;
+    if (vi < 0) return fail(ctx, LR_ERR_INVALID_ARG, "sorter_k must be one of 1, 2, 3, 4, 6, 8, 12%s");
+    if (i > 0 && vi != P->variant) return fail(ctx, LR_ERR_INVALID_ARG, "all views of a batch need the same sorter_k%s");
+    P->variant = vi;
+  }
   lr_status s = layout_for(ctx, n_views, views, &P->L);
   if (s != LR_OK) return s;
   set_capacity(P->L, workspace_bytes);
@@ -487,7 +517,7 @@ static lr_status launch_sequence(lr_ctx* ctx, const Prepared& P, cudaStream_t st
     ws.bwd_mask = bwd->exact_mask;
   }
   const int n_views = ws.n_views;
-  const bool pdl = (ctx->cfg.flags & LR_FLAG_NO_PDL) == 0;
+  const bool pdl = ctx->pdl_override >= 0 ? ctx->pdl_override != 0 : (ctx->cfg.flags & LR_FLAG_NO_PDL) == 0;
   rec(ctx, timed, 0, st);
   // the first kViewsPerLaunch descriptors travel with k_init, further ones with k_write_views
   ViewChunk chunk;
@@ -525,9 +555,9 @@ static lr_status launch_sequence(lr_ctx* ctx, const Prepared& P, cudaStream_t st
   // (lit views: neither hash nor threshold, see prepare)
   const int mode = bwd ? 2 : (P.any_lit ? 17 : ((carry ? 1 : 0) | (P.any_hash ? 4 : 0) | (ath ? 8 : 0)));
   ws.t_min = ath ? kAlphaTMin : 0.0f;
-  const int rblocks = bwd ? ctx->raster_blocks_bwd
-                          : (P.any_lit ? ctx->raster_blocks_lit : (carry ? ctx->raster_blocks_vtx : ctx->raster_blocks_flat));
-  cudaError_t e = ctx->variant->launch(mode, ws, ctx->sms * rblocks, st);
+  const VariantState& VS = ctx->vs[P.variant];
+  const int rblocks = bwd ? VS.bwd : (P.any_lit ? VS.lit : (carry ? VS.vtx : VS.flat));
+  cudaError_t e = VS.v->launch(mode, ws, ctx->sms * rblocks, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "raster launch");
   rec(ctx, timed, 6, st);
   e = launch_overflow(bwd != nullptr, ws, ctx->sms * ctx->ovf_blocks, st, pdl);
@@ -643,7 +673,8 @@ extern "C" lr_status lr_graph_launch(lr_graph* g, const lr_view* views, lr_strea
       const lr_view& a = views[i];
       const lr_view& s0 = g->shape[i];
       if (a.width != s0.width || a.height != s0.height || a.quads.num_quads != s0.quads.num_quads ||
-          a.quads.color_mode != s0.quads.color_mode || (a.target.cov_hash == nullptr) != (s0.target.cov_hash == nullptr))
+          a.quads.color_mode != s0.quads.color_mode || (a.target.cov_hash == nullptr) != (s0.target.cov_hash == nullptr) ||
+          (a.sorter_k ? a.sorter_k : ctx->cfg.sorter_k) != (s0.sorter_k ? s0.sorter_k : ctx->cfg.sorter_k))
         return fail(ctx, LR_ERR_INVALID_ARG, "graph launch views must keep the captured shapes%s");
       lr_status s = check_view(ctx, a);
       if (s != LR_OK) return s;

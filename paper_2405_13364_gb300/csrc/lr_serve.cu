@@ -8,8 +8,16 @@
 // has fewer than max_batch_views views, and launches them as one multi-view render
 // (one launch per pipeline stage for the whole batch). Up to S batches run on the GPU at
 // once, on different streams, so requests that arrive while others are being rendered are
-// admitted as soon as a slot frees up. Completion is detected with events; a batch that
-// exceeds its workspace's reference capacity is split and its requests retried alone.
+// admitted as soon as a slot frees up. A batch holds requests of one sorter capacity
+// (lr_view.sorter_k, e.g. each request's autotuned value); a batch launched while no other
+// batch is on the GPU uses programmatic dependent launch, which concurrent batches would
+// slow down. Each batch's status word is copied back on its own stream before its
+// completion event, so a finished batch needs no further synchronisation; while batches
+// run, the thread polls their events in a short spin rather than sleeping (a timed sleep
+// of a few microseconds can last tens of microseconds under the kernel's timer slack). A
+// batch that exceeds its workspace's reference capacity is split and its requests retried
+// alone.
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -63,9 +71,15 @@ struct lr_server {
   std::unordered_map<uint64_t, Req> reqs;
   uint64_t next_ticket = 1;
   bool stopping = false;
+  std::atomic<bool> submitted{false};   // a request was queued since the loop last looked
   std::thread th;
   lr_server_stats stats;
 };
+
+// the sorter capacity a request renders with
+static int request_k(const lr_server* s, const lr_view& v) {
+  return v.sorter_k ? v.sorter_k : lr_internal_config(s->inner)->sorter_k;
+}
 
 static void finish(lr_server* s, uint64_t t, int status) {
   auto it = s->reqs.find(t);
@@ -84,13 +98,11 @@ static void serve_loop(lr_server* s) {
     bool progressed = false;
     // ---- completions ---------------------------------------------------------------
     for (Slot& sl : s->slots) {
-      if (!sl.busy || cudaEventQuery(sl.done) != cudaSuccess) continue;
-      int status = LR_OK;
-      if (cudaMemcpyAsync(sl.host_ctrl, sl.ws, sizeof(Ctrl), cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
-          cudaStreamSynchronize(sl.stream) != cudaSuccess)
-        status = LR_ERR_CUDA;
-      else
-        status = sl.host_ctrl->error;
+      if (!sl.busy) continue;
+      const cudaError_t q = cudaEventQuery(sl.done);
+      if (q == cudaErrorNotReady) continue;
+      // the batch's status word was copied to host memory before its event
+      const int status = q == cudaSuccess ? sl.host_ctrl->error : LR_ERR_CUDA;
       if (status == LR_ERR_OVERFLOW && sl.tickets.size() > 1) {
         // too many references for a shared workspace: retry each request alone
         for (auto it = sl.tickets.rbegin(); it != sl.tickets.rend(); ++it) {
@@ -107,14 +119,18 @@ static void serve_loop(lr_server* s) {
     }
     if (progressed) s->done_cv.notify_all();
     // ---- admission -----------------------------------------------------------------
+    s->submitted.store(false);
     for (Slot& sl : s->slots) {
       if (sl.busy || s->queue.empty()) continue;
       views.clear();
       std::vector<uint64_t> batch;
+      int batch_k = 0;
       while (!s->queue.empty() && (int)batch.size() < s->cfg.max_batch_views) {
         const uint64_t t = s->queue.front();
         Req& r = s->reqs[t];
         if (r.alone && !batch.empty()) break;
+        if (!batch.empty() && request_k(s, r.view) != batch_k) break;   // one capacity per batch
+        batch_k = request_k(s, r.view);
         views.push_back(r.view);
         size_t need = 0;
         const lr_status st = lr_workspace_size_batch(s->inner, (int32_t)views.size(), views.data(), &need);
@@ -133,8 +149,12 @@ static void serve_loop(lr_server* s) {
         if (r.alone) break;
       }
       if (batch.empty()) continue;
+      bool others_busy = false;
+      for (const Slot& o : s->slots) others_busy |= o.busy;
+      lr_internal_set_pdl(s->inner, others_busy ? 0 : 1);
       const lr_status st = lr_render_batch(s->inner, (int32_t)views.size(), views.data(), sl.ws, sl.bytes,
                                            reinterpret_cast<lr_stream>(sl.stream));
+      lr_internal_set_pdl(s->inner, -1);
       const uint64_t t0 = now_ns();
       for (uint64_t t : batch) {
         Req& r = s->reqs[t];
@@ -146,7 +166,14 @@ static void serve_loop(lr_server* s) {
         progressed = true;
         continue;
       }
-      cudaEventRecord(sl.done, sl.stream);
+      // the status word travels back on the batch's stream, ahead of its completion event
+      if (cudaMemcpyAsync(sl.host_ctrl, sl.ws, sizeof(Ctrl), cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
+          cudaEventRecord(sl.done, sl.stream) != cudaSuccess) {
+        cudaStreamSynchronize(sl.stream);
+        for (uint64_t t : batch) finish(s, t, LR_ERR_CUDA);
+        progressed = true;
+        continue;
+      }
       sl.tickets = batch;
       sl.busy = true;
       s->stats.batches++;
@@ -157,10 +184,21 @@ static void serve_loop(lr_server* s) {
     bool any_busy = false;
     for (const Slot& sl : s->slots) any_busy |= sl.busy;
     if (s->stopping && s->queue.empty() && !any_busy) break;
-    if (any_busy)
-      s->wake.wait_for(lk, std::chrono::microseconds(s->cfg.poll_interval_us));
-    else if (s->queue.empty() && !s->stopping)
+    if (any_busy) {
+      // spin on the running batches' events for up to one poll interval, or until a new
+      // request arrives (only this thread changes the slots, so they are read unlocked)
+      lk.unlock();
+      const auto until = std::chrono::steady_clock::now() + std::chrono::microseconds(s->cfg.poll_interval_us);
+      for (;;) {
+        bool ready = false;
+        for (Slot& sl : s->slots) ready |= sl.busy && cudaEventQuery(sl.done) != cudaErrorNotReady;
+        if (ready || s->submitted.load() || std::chrono::steady_clock::now() >= until) break;
+        std::this_thread::yield();
+      }
+      lk.lock();
+    } else if (s->queue.empty() && !s->stopping) {
       s->wake.wait(lk);
+    }
   }
 }
 
@@ -252,6 +290,7 @@ extern "C" lr_status lr_submit(lr_ctx* ctx, const lr_view* view, uint64_t* ticke
     s->queue.push_back(t);
     s->stats.submitted++;
     *ticket = t;
+    s->submitted.store(true);
   }
   s->wake.notify_all();
   return LR_OK;

@@ -52,7 +52,7 @@ def test_struct_sizes_match_header_layout(lib):
     assert ctypes.sizeof(B.lr_quads) == 6 * 8
     assert ctypes.sizeof(B.lr_camera) == 18 * 4
     assert ctypes.sizeof(B.lr_target) == 5 * 8
-    assert ctypes.sizeof(B.lr_view) == 48 + 72 + 8 + 40 + 8
+    assert ctypes.sizeof(B.lr_view) == 48 + 72 + 8 + 40 + 8 + 8
 
 
 def test_struct_layouts_match_the_c_compiler(tmp_path):
