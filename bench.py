@@ -50,6 +50,17 @@ RASTER_TRAFFIC = {
 }
 RASTER_SOURCES = ("lr_raster.cuh", "lr_common.cuh")
 LANES_PER_SM_CLK = 128
+# the autotuner's candidates for the timed workloads: sorter capacity, bin size, rasteriser
+# CTAs per SM (0 = the occupancy limit)
+TUNE_KS = (1, 2, 3)
+TUNE_BINS = (16, 32, 64)
+TUNE_CTAS = (0, 2)
+
+
+def tune_label(t):
+    """k<K>[c]_b<bin>[_cta<n>] for one autotuner candidate."""
+    return (f"k{t['sorter_k']}{'c' if t['carry_colors'] else ''}_b{t['bin_size']}"
+            + (f"_cta{t['raster_ctas_per_sm']}" if t["raster_ctas_per_sm"] else ""))
 
 
 def _workloads():
@@ -165,7 +176,7 @@ class ClockSampler:
                 "samples": len(self.samples), "period_ms": self.period_ms}
 
 
-def frame_benchmark(P, torch, scene, k, carry, steps, warmup, flush, dev, dist=None):
+def frame_benchmark(P, torch, scene, k, carry, steps, warmup, flush, dev, dist=None, bin_size=32, ctas=0):
     """Device-timed frames of one workload: a renderer without per-stage events renders
     `steps` frames (L2 flushed before each, outside the events; CUDA events on the stream
     around each frame), then a second renderer that records an event between stages gives
@@ -173,8 +184,8 @@ def frame_benchmark(P, torch, scene, k, carry, steps, warmup, flush, dev, dist=N
     stage means, the outputs and view of the timed renderer)."""
     W, H = scene.width, scene.height
     ds = P.DeviceScene.from_scene(scene, device=dev)
-    r = P.Renderer(sorter_k=k, carry_colors=carry)
-    rt = P.Renderer(sorter_k=k, timing=True, carry_colors=carry)
+    r = P.Renderer(sorter_k=k, carry_colors=carry, bin_size=bin_size, raster_ctas_per_sm=ctas)
+    rt = P.Renderer(sorter_k=k, timing=True, carry_colors=carry, bin_size=bin_size, raster_ctas_per_sm=ctas)
     out = r.make_outputs(W, H)
     view = r.view_struct(ds, W, H, out)
     view_t = rt.view_struct(ds, W, H, out)
@@ -244,19 +255,21 @@ def particles_benchmark(P, torch, args, flush, dev, sm_count, hbm_gbs):
     from paper_2405_13364_gb300 import autotune
     scene = scenegen.config_particles_1080p()
     ds = P.DeviceScene.from_scene(scene, device=dev)
-    tuned = autotune.tune(ds, scene.width, scene.height, ks=(1, 2, 3), ctas_per_sm=(0,), reps=3, device=dev)
+    tuned = autotune.tune(ds, scene.width, scene.height, ks=TUNE_KS, ctas_per_sm=TUNE_CTAS, reps=3, device=dev,
+                          bin_sizes=TUNE_BINS, use_cache=False)
     del ds
     k, carry = tuned["sorter_k"], bool(tuned.get("carry_colors"))
     ms, st0, stages, sampler, (r, _, _, _) = frame_benchmark(P, torch, scene, k, carry, min(args.steps, 20),
-                                                             args.warmup, flush, dev)
+                                                             args.warmup, flush, dev, None, tuned["bin_size"],
+                                                             tuned["raster_ctas_per_sm"])
     r.close()
     frags = st0["fragments"]
     clocks = sampler.summary()
     return {"workload": WORKLOADS["particles"][0], "frame": f"{scene.width}x{scene.height}",
             "quads": scene.num_quads, "fragments_per_frame": frags, "ms_per_frame": round(ms, 4),
             "gfrag_s": round(frags / (ms * 1e-3) / 1e9, 3), "sorter_k": k, "carry_colors": carry,
-            "autotune_ms": {f"k{t['sorter_k']}{'c' if t['carry_colors'] else ''}": round(t["ms"], 4)
-                            for t in tuned["table"]},
+            "bin_size": tuned["bin_size"], "raster_ctas_per_sm": tuned["raster_ctas_per_sm"],
+            "autotune_ms": {tune_label(t): round(t["ms"], 4) for t in tuned["table"]},
             "stage_ms": stages, "overflow_pixels": st0["overflow_pixels"], "bins_high": st0["bins_high"],
             "sort_bins": st0["sort_bins"],
             "roofline": raster_roofline("particles", k, carry, frags, stages["raster"], sm_count,
@@ -337,7 +350,7 @@ def serving_benchmark(P, torch, num_requests=256, rate_hz=200.0, seed=0):
         key = autotune.workload_key(q["width"], q["height"], sc.num_quads, sc.color_mode)
         if key not in tuned_buckets:
             tuned_buckets[key] = autotune.tune(sc, q["width"], q["height"], ks=(1, 2, 3), reps=3,
-                                               carry=(False,))["sorter_k"]
+                                               carry=(False,), use_cache=False)["sorter_k"]
         ks.append(tuned_buckets[key])
     frags = 0
     # ---- sequential: one lr_render per request, in arrival order, one at a time -----------
@@ -523,13 +536,16 @@ def run_gpu(args):
         # the sorter capacity K picked by the autotuner for this workload (any K gives the
         # same exact result; it only moves pixels between the sorter and the exact path)
         from paper_2405_13364_gb300 import autotune
-        tuned = autotune.tune(ds, W, H, ks=(1, 2, 3, 4), ctas_per_sm=(0,), reps=3, device=dev)
+        tuned = autotune.tune(ds, W, H, ks=TUNE_KS, ctas_per_sm=TUNE_CTAS, reps=3, device=dev,
+                              bin_sizes=TUNE_BINS, use_cache=False)
         args.k = tuned["sorter_k"]
     carry = bool(tuned and tuned.get("carry_colors"))
+    bin_size = tuned["bin_size"] if tuned else 32
+    ctas = tuned["raster_ctas_per_sm"] if tuned else 0
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     ms_frame, st0, stages, sampler, (r, ds, out, view) = frame_benchmark(
-        P, torch, scene, args.k, carry, args.steps, args.warmup, flush, dev, dist)
+        P, torch, scene, args.k, carry, args.steps, args.warmup, flush, dev, dist, bin_size, ctas)
     frags = st0["fragments"]
     from paper_2405_13364_gb300 import replicas
     ms_step = replicas.max_over_ranks(ms_frame, dist, dev)
@@ -632,7 +648,8 @@ def run_gpu(args):
     # the exact frame's, and the largest deviation from the exact image (at most 1/128) ---
     alpha_threshold = None
     if world == 1:
-        ra = P.Renderer(sorter_k=args.k, carry_colors=carry, alpha_threshold=True)
+        ra = P.Renderer(sorter_k=args.k, carry_colors=carry, alpha_threshold=True, bin_size=bin_size,
+                        raster_ctas_per_sm=ctas)
         oa = ra.make_outputs(W, H)
         va = ra.view_struct(ds, W, H, oa)
         ra.render_views([va])
@@ -660,7 +677,7 @@ def run_gpu(args):
     # ---- multisampling (4 samples per pixel, every sample an exact composite) ------------
     msaa = None
     if world == 1:
-        rm = P.Renderer(sorter_k=args.k, carry_colors=carry)
+        rm = P.Renderer(sorter_k=args.k, carry_colors=carry, bin_size=bin_size, raster_ctas_per_sm=ctas)
         rm.render_msaa(ds, W, H, samples=4)           # sizes the workspace
         stm = rm.stats()
         for _ in range(args.warmup):
@@ -686,7 +703,7 @@ def run_gpu(args):
     if world == 1 and args.workload == "layers":
         lscene = scenegen.wavy_layers(color_mode=scenegen.COLOR_LIT)
         lds = P.DeviceScene.from_scene(lscene, device=dev)
-        rl = P.Renderer(sorter_k=args.k, carry_colors=carry)
+        rl = P.Renderer(sorter_k=args.k, carry_colors=carry, bin_size=bin_size, raster_ctas_per_sm=ctas)
         rl.set_lighting(lscene.light[:3], lscene.light[3])
         ol = rl.make_outputs(W, H)
         vl = rl.view_struct(lds, W, H, ol)
@@ -739,8 +756,8 @@ def run_gpu(args):
         "config": {"workload": WORKLOADS[args.workload][0], "frame": f"{W}x{H}", "quads": scene.num_quads,
                    "fragments_per_frame": frags, "sorter_k": args.k,
                    "carry_colors": carry,
-                   "autotune_ms": None if tuned is None else
-                   {f"k{t['sorter_k']}{'c' if t['carry_colors'] else ''}": round(t["ms"], 4) for t in tuned["table"]},
+                   "bin_size": bin_size, "raster_ctas_per_sm": ctas,
+                   "autotune_ms": None if tuned is None else {tune_label(t): round(t["ms"], 4) for t in tuned["table"]},
                    "l2": "flushed before every step (512 MiB write, outside the timed events)",
                    "parallelism": f"replicas x{world} (one frame per GPU per step)"},
         "stage_ms": stages,

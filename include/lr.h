@@ -91,6 +91,11 @@ typedef struct {
   int32_t ref_factor;        /* bin-reference capacity per quad in the workspace; default 4 */
   int32_t flags;             /* LR_FLAG_* */
   int32_t device;            /* CUDA device ordinal; -1 or 0 = current device */
+  int32_t bin_size;          /* pixels per side of the binning stage's square bins: 16, 32 or
+                                64 (Sec. 2, Stage 2 uses 32; Sec. 4 proposes 64 for sparse
+                                and 16 for dense regions); default 32. Any bin size gives the
+                                same exact image: it changes how many (quad, bin) references
+                                binning makes and how large the per-bin depth sorts are. */
 } lr_config;
 
 /* A quad scene (Sec. 2: quads, not triangles, are the input primitive). Device memory. */

@@ -70,6 +70,7 @@ static const RasterVariant kVariants[] = {
 };
 
 struct Layout {
+  int bin_log2 = kBinLog2Default;
   size_t ctrl, views, rec, rec_rect, rec_info, rec_rep, bin_count, bin_off, bin_cursor, bin_order, chunk_span;
   size_t refs, refs_tmp, ref_hb, ovf_list, total;
   long long total_quads = 0, total_pix = 0, refs_cap = 0;
@@ -81,10 +82,12 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Workspace layout. The two bin-reference arrays come last; their capacity is whatever the
 // workspace holds beyond the fixed part (set_capacity), so a caller that hit
 // LR_ERR_OVERFLOW can pass a larger workspace without recreating the context.
-static Layout make_layout(int n, const long long* Q, const int* W, const int* H) {
+static Layout make_layout(int n, const long long* Q, const int* W, const int* H, int lg) {
   Layout L;
+  L.bin_log2 = lg;
+  const int B = 1 << lg;
   for (int i = 0; i < n; ++i) {
-    const int nbx = (W[i] + kBin - 1) / kBin, nby = (H[i] + kBin - 1) / kBin;
+    const int nbx = (W[i] + B - 1) / B, nby = (H[i] + B - 1) / B;
     L.total_quads += Q[i];
     L.total_pix += (long long)W[i] * H[i];
     L.total_bins += nbx * nby;
@@ -115,18 +118,20 @@ static long long default_refs(const Layout& L, int ref_factor) {
   return std::min((long long)ref_factor * L.total_quads + 64LL * L.total_bins + 1024, kMaxRefs);
 }
 
-// per reference: the sort key, its merge buffer slot and its word of the half-block
-// bitmap (plus up to 32 padding words per bin)
+// per reference: the sort key, its merge buffer slot and its mw words of the half-block
+// bitmap (plus up to mrows padding words per bin)
 static size_t bytes_for_refs(const Layout& L, long long refs) {
+  const size_t mw = (size_t)bin_mw(L.bin_log2), mrows = (size_t)bin_mrows(L.bin_log2);
   return L.refs + align256(sizeof(unsigned long long) * (size_t)refs) * 2 +
-         align256(sizeof(uint32_t) * ((size_t)refs + 32 * (size_t)L.total_bins));
+         align256(sizeof(uint32_t) * (mw * (size_t)refs + mrows * (size_t)L.total_bins));
 }
 
 // capacity from the bytes available, placing refs_tmp and ref_hb after refs
 static void set_capacity(Layout& L, size_t ws_bytes) {
   long long cap = 0;
-  const size_t fixed = L.refs + 32 * sizeof(uint32_t) * (size_t)L.total_bins + 1024;
-  if (ws_bytes > fixed) cap = (long long)((ws_bytes - fixed) / (2 * sizeof(unsigned long long) + sizeof(uint32_t)));
+  const size_t mw = (size_t)bin_mw(L.bin_log2), mrows = (size_t)bin_mrows(L.bin_log2);
+  const size_t fixed = L.refs + mrows * sizeof(uint32_t) * (size_t)L.total_bins + 1024;
+  if (ws_bytes > fixed) cap = (long long)((ws_bytes - fixed) / (2 * sizeof(unsigned long long) + mw * sizeof(uint32_t)));
   cap = std::min(cap, kMaxRefs);
   cap &= ~63LL;
   while (cap > 0 && bytes_for_refs(L, cap) > ws_bytes) cap -= 64;
@@ -147,6 +152,7 @@ static Ws make_ws(const Layout& L, void* base, int n_views) {
   w.total_quads = L.total_quads;
   w.total_pix = L.total_pix;
   w.refs_cap = L.refs_cap;
+  w.bin_log2 = L.bin_log2;
   w.rec = reinterpret_cast<int4*>(b + L.rec);
   w.rec_rect = reinterpret_cast<uint2*>(b + L.rec_rect);
   w.rec_info = reinterpret_cast<uint32_t*>(b + L.rec_info);
@@ -181,6 +187,7 @@ struct lr_ctx {
   VariantState vs[sizeof(kVariants) / sizeof(kVariants[0])];
   int variant = 0;             // index of the context's default sorter capacity in vs
   int pdl_override = -1;       // -1: as cfg.flags say; 0 / 1: this render without / with PDL
+  int bin_log2 = kBinLog2Default;   // from cfg.bin_size
   float light[4] = {0.f, 0.f, 1.f, 0.25f};   // LR_COLOR_LIT: unit direction toward the light, ambient
   int ovf_blocks = 1;
   // last render, for lr_get_stats
@@ -223,7 +230,9 @@ extern "C" lr_status lr_create(const lr_config* config, lr_ctx** out_ctx) {
   if (g.max_height <= 0) g.max_height = 2048;
   if (g.sorter_k <= 0) g.sorter_k = 3;
   if (g.ref_factor <= 0) g.ref_factor = 4;
-  if (g.max_width > 65535 || g.max_height > 65535 || g.raster_ctas_per_sm < 0) {
+  if (g.bin_size <= 0) g.bin_size = 1 << kBinLog2Default;
+  c->bin_log2 = g.bin_size == 16 ? 4 : (g.bin_size == 32 ? 5 : (g.bin_size == 64 ? 6 : -1));
+  if (g.max_width > 65535 || g.max_height > 65535 || g.raster_ctas_per_sm < 0 || c->bin_log2 < 0) {
     delete c;
     return LR_ERR_INVALID_ARG;
   }
@@ -342,7 +351,7 @@ static lr_status layout_for(lr_ctx* c, int n, const lr_view* views, Layout* out)
     H[i] = views[i].height;
     total_pix += (long long)W[i] * H[i];
   }
-  *out = make_layout(n, Q.data(), W.data(), H.data());
+  *out = make_layout(n, Q.data(), W.data(), H.data(), c->bin_log2);
   if (out->total_quads > 0x7FFFFFFFLL || total_pix > 0xFFFFFFFFLL)
     return fail(c, LR_ERR_TOO_LARGE, "batch too large%s");
   return LR_OK;
@@ -354,7 +363,7 @@ extern "C" lr_status lr_workspace_size(const lr_ctx* ctx, int64_t num_quads, int
   if (width > ctx->cfg.max_width || height > ctx->cfg.max_height) return LR_ERR_TOO_LARGE;
   const long long q = num_quads;
   const int w = width, h = height;
-  Layout L = make_layout(1, &q, &w, &h);
+  Layout L = make_layout(1, &q, &w, &h, ctx->bin_log2);
   *out_bytes = bytes_for_refs(L, default_refs(L, ctx->cfg.ref_factor));
   return LR_OK;
 }
@@ -419,7 +428,8 @@ struct Prepared {
 };
 
 static void describe_views(int32_t n_views, const lr_view* views, std::vector<ViewDev>& vd, bool* any_vertex,
-                           bool* any_hash, bool* any_lit, const float* light) {
+                           bool* any_hash, bool* any_lit, const float* light, int lg) {
+  const int B = 1 << lg;
   vd.resize(n_views);
   long long qb = 0, pb = 0;
   int bb = 0, cb = 0;
@@ -455,8 +465,8 @@ static void describe_views(int32_t n_views, const lr_view* views, std::vector<Vi
     d.color_mode = v.quads.color_mode;
     d.width = v.width;
     d.height = v.height;
-    d.nbx = (v.width + kBin - 1) / kBin;
-    d.nby = (v.height + kBin - 1) / kBin;
+    d.nbx = (v.width + B - 1) / B;
+    d.nby = (v.height + B - 1) / B;
     d.quad_base = qb;
     d.pix_base = pb;
     d.bin_base = bb;
@@ -496,7 +506,7 @@ static lr_status prepare(lr_ctx* ctx, int32_t n_views, const lr_view* views, voi
   if (s != LR_OK) return s;
   set_capacity(P->L, workspace_bytes);
   if (P->L.refs_cap < 1024) return fail(ctx, LR_ERR_OOM, "workspace too small (see lr_workspace_size)%s");
-  describe_views(n_views, views, P->vd, &P->any_vertex, &P->any_hash, &P->any_lit, ctx->light);
+  describe_views(n_views, views, P->vd, &P->any_vertex, &P->any_hash, &P->any_lit, ctx->light, ctx->bin_log2);
   if (P->any_lit && (P->any_hash || (ctx->cfg.flags & LR_FLAG_ALPHA_THRESHOLD)))
     return fail(ctx, LR_ERR_UNSUPPORTED, "lit colours with coverage hashes or the alpha threshold%s");
   P->ws = make_ws(P->L, workspace, n_views);
@@ -682,7 +692,7 @@ extern "C" lr_status lr_graph_launch(lr_graph* g, const lr_view* views, lr_strea
     std::vector<ViewDev> vd;
     bool any_vertex = false, any_hash = false, any_lit = false;
     // replays keep the light the graph was captured with
-    describe_views(n, views, vd, &any_vertex, &any_hash, &any_lit, g->P.vd[0].light);
+    describe_views(n, views, vd, &any_vertex, &any_hash, &any_lit, g->P.vd[0].light, ctx->bin_log2);
     memcpy(g->staging[b], vd.data(), sizeof(ViewDev) * (size_t)n);
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -798,7 +808,7 @@ extern "C" lr_status lr_workspace_size_msaa(const lr_ctx* ctx, int64_t num_quads
   if (width > ctx->cfg.max_width || height > ctx->cfg.max_height) return LR_ERR_TOO_LARGE;
   std::vector<long long> Q(n_samples, num_quads);
   std::vector<int> W(n_samples, width), H(n_samples, height);
-  Layout L = make_layout(n_samples, Q.data(), W.data(), H.data());
+  Layout L = make_layout(n_samples, Q.data(), W.data(), H.data(), ctx->bin_log2);
   if (L.total_quads > 0x7FFFFFFFLL || L.total_pix > 0xFFFFFFFFLL) return LR_ERR_TOO_LARGE;
   *out_bytes = msaa_image_bytes(n_samples, width, height) + bytes_for_refs(L, default_refs(L, ctx->cfg.ref_factor));
   return LR_OK;

@@ -35,7 +35,7 @@ namespace lr {
 // Conservative test whether a triangle of a quad can cover a pixel centre of bin (bx, by):
 // false only if one edge is negative (after the fill-rule bias) at all four corner pixel
 // centres of the bin rectangle clipped to the triangle's pixel AABB and the screen.
-__device__ bool tri_may_touch_bin(const int X[4], const int Y[4], int t, int bx, int by, int W, int H) {
+__device__ bool tri_may_touch_bin(const int X[4], const int Y[4], int t, int bx, int by, int W, int H, int lg) {
   int a = 0, b = t == 0 ? 1 : 2, c = t == 0 ? 2 : 3;
   long long A = area2(X[a], Y[a], X[b], Y[b], X[c], Y[c]);
   if (A == 0) return false;
@@ -43,10 +43,10 @@ __device__ bool tri_may_touch_bin(const int X[4], const int Y[4], int t, int bx,
   const int vx[3] = {X[a], X[b], X[c]}, vy[3] = {Y[a], Y[b], Y[c]};
   const int xmin = min(vx[0], min(vx[1], vx[2])), xmax = max(vx[0], max(vx[1], vx[2]));
   const int ymin = min(vy[0], min(vy[1], vy[2])), ymax = max(vy[0], max(vy[1], vy[2]));
-  const int x0 = max(max(ceil_div256((long long)xmin - 128), 0), bx << kBinLog2);
-  const int x1 = min(min(floor_div256((long long)xmax - 128), W - 1), (bx << kBinLog2) + kBin - 1);
-  const int y0 = max(max(ceil_div256((long long)ymin - 128), 0), by << kBinLog2);
-  const int y1 = min(min(floor_div256((long long)ymax - 128), H - 1), (by << kBinLog2) + kBin - 1);
+  const int x0 = max(max(ceil_div256((long long)xmin - 128), 0), bx << lg);
+  const int x1 = min(min(floor_div256((long long)xmax - 128), W - 1), ((bx + 1) << lg) - 1);
+  const int y0 = max(max(ceil_div256((long long)ymin - 128), 0), by << lg);
+  const int y1 = min(min(floor_div256((long long)ymax - 128), H - 1), ((by + 1) << lg) - 1);
   if (x0 > x1 || y0 > y1) return false;
   const long long cx[2] = {256LL * x0 + 128, 256LL * x1 + 128};
   const long long cy[2] = {256LL * y0 + 128, 256LL * y1 + 128};
@@ -71,8 +71,8 @@ __device__ __forceinline__ bool quad_may_touch_bin(const Ws& ws, long long q, ui
                                                    int by, int W, int H) {
   const int4 a = ws.rec[4 * q], b = ws.rec[4 * q + 1];
   const int X[4] = {a.x, a.z, b.x, b.z}, Y[4] = {a.y, a.w, b.y, b.w};
-  return ((info & kInfoTri0) && tri_may_touch_bin(X, Y, 0, bx, by, W, H)) ||
-         ((info & kInfoTri1) && tri_may_touch_bin(X, Y, 1, bx, by, W, H));
+  return ((info & kInfoTri0) && tri_may_touch_bin(X, Y, 0, bx, by, W, H, ws.bin_log2)) ||
+         ((info & kInfoTri1) && tri_may_touch_bin(X, Y, 1, bx, by, W, H, ws.bin_log2));
 }
 
 // Per-bin representative depth of a quad that spans several bins.
@@ -95,6 +95,7 @@ template <typename F>
 __device__ __forceinline__ void for_each_ref(const Ws& ws, const ViewDev& V, long long q0, long long q1,
                                              F&& f) {
   const int lane = threadIdx.x & 31;
+  const int lg = ws.bin_log2;
   for (long long base = q0 + (threadIdx.x & ~31); base < q1; base += blockDim.x) {
     const long long q = base + lane;
     const bool in = q < q1;
@@ -104,8 +105,8 @@ __device__ __forceinline__ void for_each_ref(const Ws& ws, const ViewDev& V, lon
     const bool vis = in && rect.x != kRectInvisible;
     const int px0 = rect.x & 0xffff, px1 = rect.x >> 16, py0 = rect.y & 0xffff, py1 = rect.y >> 16;
     if (vis && !(info & kInfoLarge)) {
-      for (int by = py0 >> kBinLog2; by <= (py1 >> kBinLog2); ++by)
-        for (int bx = px0 >> kBinLog2; bx <= (px1 >> kBinLog2); ++bx) f(q, by * V.nbx + bx, bx, by, rect, info);
+      for (int by = py0 >> lg; by <= (py1 >> lg); ++by)
+        for (int bx = px0 >> lg; bx <= (px1 >> lg); ++bx) f(q, by * V.nbx + bx, bx, by, rect, info);
     }
     unsigned large = __ballot_sync(0xffffffffu, vis && (info & kInfoLarge));
     while (large) {
@@ -114,8 +115,8 @@ __device__ __forceinline__ void for_each_ref(const Ws& ws, const ViewDev& V, lon
       const long long lq = __shfl_sync(0xffffffffu, q, src);
       const uint2 lr = make_uint2(__shfl_sync(0xffffffffu, rect.x, src), __shfl_sync(0xffffffffu, rect.y, src));
       const uint32_t li = __shfl_sync(0xffffffffu, info, src);
-      const int bx0 = (lr.x & 0xffff) >> kBinLog2, bx1 = (lr.x >> 16) >> kBinLog2;
-      const int by0 = (lr.y & 0xffff) >> kBinLog2, by1 = (lr.y >> 16) >> kBinLog2;
+      const int bx0 = (lr.x & 0xffff) >> lg, bx1 = (lr.x >> 16) >> lg;
+      const int by0 = (lr.y & 0xffff) >> lg, by1 = (lr.y >> 16) >> lg;
       const int bw = bx1 - bx0 + 1, nb = bw * (by1 - by0 + 1);
       for (int i = lane; i < nb; i += 32) {
         const int bx = bx0 + i % bw, by = by0 + i / bw;
@@ -225,7 +226,7 @@ __global__ __launch_bounds__(1024) void k_bin_scan(Ws ws) {
   if (tid == 0) {
     ws.bin_off[n] = (uint32_t)min(carry, (unsigned long long)ws.refs_cap);
     ws.ctrl->refs_total = carry;
-    ws.ctrl->raster_items = (unsigned long long)n * kHbPerBin;
+    ws.ctrl->raster_items = (unsigned long long)n * bin_hb(ws.bin_log2);
     if (carry > (unsigned long long)ws.refs_cap) set_error(ws.ctrl, LR_ERR_OVERFLOW);
   }
   // statistics
@@ -276,14 +277,15 @@ __global__ __launch_bounds__(kBinThreads, 5) void k_bin_scatter(Ws ws) {
   }
   for_each_ref(ws, V, q0, q1, [&](long long q, int b, int bx, int by, uint2 rect, uint32_t info) {
     const uint32_t slot = smem ? atomicAdd(&hist[b], 1u) : atomicAdd(&ws.bin_cursor[V.bin_base + b], 1u);
-    const int x0 = max((int)(rect.x & 0xffff), bx << kBinLog2);
-    const int x1 = min((int)(rect.x >> 16), (bx << kBinLog2) + kBin - 1);
-    const int y0 = max((int)(rect.y & 0xffff), by << kBinLog2);
-    const int y1 = min((int)(rect.y >> 16), (by << kBinLog2) + kBin - 1);
+    const int lg = ws.bin_log2;
+    const int x0 = max((int)(rect.x & 0xffff), bx << lg);
+    const int x1 = min((int)(rect.x >> 16), ((bx + 1) << lg) - 1);
+    const int y0 = max((int)(rect.y & 0xffff), by << lg);
+    const int y1 = min((int)(rect.y >> 16), ((by + 1) << lg) - 1);
     // a quad inside one bin, or of constant depth: its per-quad value; else the plane at its
     // box clipped to this bin
-    const bool one_bin = ((rect.x & 0xffff) >> kBinLog2) == ((rect.x >> 16) >> kBinLog2) &&
-                         ((rect.y & 0xffff) >> kBinLog2) == ((rect.y >> 16) >> kBinLog2);
+    const bool one_bin = ((rect.x & 0xffff) >> lg) == ((rect.x >> 16) >> lg) &&
+                         ((rect.y & 0xffff) >> lg) == ((rect.y >> 16) >> lg);
     const float rep = (one_bin || (info & kInfoFlatDepth)) ? ws.rec_rep[q] : rep_depth(ws, q, info, x0, x1, y0, y1);
     if (slot < (uint32_t)ws.refs_cap) ws.refs[slot] = ref_key(rep, q);
   });
@@ -310,47 +312,54 @@ __device__ void cta_merge(const unsigned long long* a, int na, const unsigned lo
   }
 }
 
-// The bin's transposed half-block bitmap (hb_row): for each sorted reference, the 32-bit
-// mask of the bin's 8x4 half-blocks (bit hy * 4 + hx) that the quad's pixel AABB overlaps,
-// computed one warp per 32 references and transposed across the warp, so that row h, word
-// w holds the bits of references 32 w .. 32 w + 31 for half-block h. The rasteriser then
-// reads a half-block's candidates with one coalesced load per 1024 references.
-// When the bitmap fits `stage` (shared memory, stage_words 32-bit words), the transposed
-// words are assembled there and copied out row by row with coalesced stores; otherwise each
-// lane stores its word of a row directly.
+// The bin's transposed half-block bitmap (hb_row): for each sorted reference, the mask of
+// the bin's 8x4 half-blocks (bit hy * cols + hx, in mw 32-bit words) that the quad's pixel
+// AABB overlaps, computed one warp per 32 references and transposed across the warp word by
+// word, so that row h, word w holds the bits of references 32 w .. 32 w + 31 for half-block
+// h. The rasteriser then reads a half-block's candidates with one coalesced load per 1024
+// references. When the bitmap fits `stage` (shared memory, stage_words 32-bit words), the
+// transposed words are assembled there and copied out row by row with coalesced stores;
+// otherwise each lane stores its word of a row directly.
 __device__ void write_hb_bitmap(const Ws& ws, const unsigned long long* r, int n, int bin, uint32_t* stage,
                                 int stage_words) {
   const int v = view_of_bin(ws.views, ws.n_views, bin);
   const ViewDev& V = ws.views[v];
   const int b = bin - V.bin_base;
-  const int x0 = (b % V.nbx) << kBinLog2, y0 = (b / V.nbx) << kBinLog2;
+  const int lg = ws.bin_log2, B = 1 << lg;
+  const int cols = bin_hb_cols(lg), mw = bin_mw(lg), mrows = bin_mrows(lg);
+  const int rpw = 32 / cols;                              // half-block rows per mask word
+  // bit i * cols for every row i of a word: the row pattern's replication
+  const uint32_t rep = cols == 8 ? 0x01010101u : (cols == 4 ? 0x11111111u : 0x55555555u);
+  const int x0 = (b % V.nbx) << lg, y0 = (b / V.nbx) << lg;
   const int nw = (n + 31) >> 5;
   const int lane = threadIdx.x & 31;
-  uint32_t* bm = ws.ref_hb + (r - ws.refs) + 32 * (size_t)bin;
-  const bool staged = 32 * nw <= stage_words;
+  uint32_t* bm = ws.ref_hb + (size_t)mw * (size_t)(r - ws.refs) + (size_t)mrows * (size_t)bin;
+  const bool staged = mrows * nw <= stage_words;
   uint32_t* dst = staged ? stage : bm;
   for (int w = threadIdx.x >> 5; w < nw; w += blockDim.x >> 5) {
     const int i = 32 * w + lane;
-    uint32_t mask = 0;
+    int hx0 = 1, hx1 = 0, hy0 = 1, hy1 = 0;                // empty unless the box meets the bin
     const uint32_t rec = i < n ? ~(uint32_t)r[i] : 0xFFFFFFFFu;
     if (rec < (uint64_t)ws.total_quads) {
       const uint2 rc = ws.rec_rect[rec];
-      const int px0 = max((int)(rc.x & 0xffff), x0) - x0, px1 = min((int)(rc.x >> 16), x0 + kBin - 1) - x0;
-      const int py0 = max((int)(rc.y & 0xffff), y0) - y0, py1 = min((int)(rc.y >> 16), y0 + kBin - 1) - y0;
+      const int px0 = max((int)(rc.x & 0xffff), x0) - x0, px1 = min((int)(rc.x >> 16), x0 + B - 1) - x0;
+      const int py0 = max((int)(rc.y & 0xffff), y0) - y0, py1 = min((int)(rc.y >> 16), y0 + B - 1) - y0;
       if (px0 <= px1 && py0 <= py1) {
-        const int hx0 = px0 / kHbW, hx1 = px1 / kHbW, hy0 = py0 / kHbH, hy1 = py1 / kHbH;
-        // the half-block columns hx0..hx1 (4 bits) replicated into rows hy0..hy1 (a nibble
-        // per row): a product, since a row's nibble never carries into the next
-        const uint32_t row = ((2u << hx1) - 1u) & ~((1u << hx0) - 1u);
-        const uint32_t rows = 0x11111111u & ((2u << (4 * hy1)) - 1u) & ~((1u << (4 * hy0)) - 1u);
-        mask = row * rows;
+        hx0 = px0 / kHbW; hx1 = px1 / kHbW; hy0 = py0 / kHbH; hy1 = py1 / kHbH;
       }
     }
-    dst[(size_t)lane * nw + w] = warp_transpose32(mask, lane);
+    // the half-block columns hx0..hx1 replicated into the rows hy0..hy1 that fall in mask
+    // word m: a product, since a row's pattern never carries into the next row
+    const uint32_t row = hx0 <= hx1 ? ((2u << hx1) - 1u) & ~((1u << hx0) - 1u) : 0u;
+    for (int m = 0; m < mw; ++m) {
+      const int a = max(hy0 - m * rpw, 0), c = min(hy1 - m * rpw, rpw - 1);
+      const uint32_t rows = a <= c ? rep & ((2u << (c * cols)) - 1u) & ~((1u << (a * cols)) - 1u) : 0u;
+      dst[(size_t)(32 * m + lane) * nw + w] = warp_transpose32(row * rows, lane);
+    }
   }
   if (staged) {
     __syncthreads();
-    for (int i = threadIdx.x; i < 32 * nw; i += blockDim.x) bm[i] = stage[i];
+    for (int i = threadIdx.x; i < mrows * nw; i += blockDim.x) bm[i] = stage[i];
   }
 }
 
@@ -526,14 +535,20 @@ __device__ __forceinline__ void cta_merge_sort_smem(unsigned long long* g, int n
   for (int i = t; i < n; i += T) g[i] = src[i];
 }
 
-// Whether a bin (a 32x32-pixel tile) is rasterised by this render (its view's owned-tile
-// set, when it has one).
+// Whether a bin is rasterised by this render: with an owned-tile set, whether any 32x32-pixel
+// tile the bin covers is owned (a bin of 16 pixels lies in one tile, one of 64 spans up to
+// four).
 __device__ __forceinline__ bool bin_owned(const Ws& ws, int bin) {
   const int v = view_of_bin(ws.views, ws.n_views, bin);
   const ViewDev& V = ws.views[v];
   if (!V.owned) return true;
-  const int b = bin - V.bin_base;
-  return tile_owned(V, (b % V.nbx) << kBinLog2, (b / V.nbx) << kBinLog2);
+  const int b = bin - V.bin_base, lg = ws.bin_log2;
+  const int x0 = (b % V.nbx) << lg, y0 = (b / V.nbx) << lg;
+  const int x1 = min(x0 + (1 << lg), V.width) - 1, y1 = min(y0 + (1 << lg), V.height) - 1;
+  for (int ty = y0 >> kTileLog2; ty <= (y1 >> kTileLog2); ++ty)
+    for (int tx = x0 >> kTileLog2; tx <= (x1 >> kTileLog2); ++tx)
+      if (tile_owned(V, tx << kTileLog2, ty << kTileLog2)) return true;
+  return false;
 }
 
 __global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {

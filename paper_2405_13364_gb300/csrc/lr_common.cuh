@@ -15,10 +15,19 @@
 
 namespace lr {
 
-constexpr int kBinLog2 = 5;                 // 32x32-pixel bins (Sec. 2, Stage 2)
-constexpr int kBin = 1 << kBinLog2;
+constexpr int kBinLog2Default = 5;          // 32x32-pixel bins (Sec. 2, Stage 2); 16 and 64
+                                            // are the alternatives (lr_config.bin_size)
 constexpr int kHbW = 8, kHbH = 4;           // 8x4 half-blocks (Sec. 2, Stage 3)
-constexpr int kHbPerBin = (kBin / kHbW) * (kBin / kHbH);   // 32
+constexpr int kTileLog2 = 5;                // 32x32-pixel tiles of lr_view.owned_tiles
+
+// Geometry of a bin of 2^lg pixels per side (lg = 4, 5 or 6): its 8x4 half-blocks, cols
+// per row and rows, numbered hy * cols + hx; the transposed half-block bitmap of a bin
+// keeps mrows >= 32 rows (a multiple of 32, so that a reference's half-block mask is mw
+// whole 32-bit words).
+__host__ __device__ __forceinline__ int bin_hb(int lg) { return 1 << (2 * lg - 5); }        // 8, 32, 128
+__host__ __device__ __forceinline__ int bin_hb_cols(int lg) { return 1 << (lg - 3); }       // 2, 4, 8
+__host__ __device__ __forceinline__ int bin_mrows(int lg) { return bin_hb(lg) < 32 ? 32 : bin_hb(lg); }
+__host__ __device__ __forceinline__ int bin_mw(int lg) { return bin_mrows(lg) >> 5; }       // 1, 1, 4
 constexpr float kGuardPx = 16384.0f;        // guard band, pixels
 constexpr int kSortSmemCap = 2048;          // bins below this many refs: k_bin_sort (256 threads)
 constexpr int kSortBigCap = 8192;           // k_bin_sort_big sorts runs of up to this many refs
@@ -34,7 +43,7 @@ constexpr size_t kSortBigSmemBytes =
     (size_t)kBucketBigCap * 8 + (2 * (size_t)kBucketsBig + 2) * 4 > 2 * (size_t)kSortBigCap * 8
         ? (size_t)kBucketBigCap * 8 + (2 * (size_t)kBucketsBig + 2) * 4
         : 2 * (size_t)kSortBigCap * 8;
-constexpr int kHistSmemBins = 5120;         // shared-memory bin counters per CTA (Sec. 2 Stage 2)
+constexpr int kHistSmemBins = 8192;         // shared-memory bin counters per CTA (Sec. 2 Stage 2)
 constexpr int kChunkQuads = 1024;           // quads per binning CTA
 constexpr int kBinThreads = 256;            // threads per binning CTA
 constexpr int kSmallBins = 4;               // AABB-counted up to kSmallBins x kSmallBins bins
@@ -87,7 +96,7 @@ struct ViewDev {
 // the view has no owned-tile set).
 __device__ __forceinline__ bool tile_owned(const ViewDev& V, int px, int py) {
   if (!V.owned) return true;
-  const int t = (py >> 5) * ((V.width + 31) >> 5) + (px >> 5);
+  const int t = (py >> kTileLog2) * ((V.width + 31) >> kTileLog2) + (px >> kTileLog2);
   return (__ldg(V.owned + (t >> 5)) >> (t & 31)) & 1u;
 }
 
@@ -186,6 +195,7 @@ struct Ws {
   long long total_quads;
   long long total_pix;
   long long refs_cap;
+  int bin_log2;              // bins of 2^bin_log2 x 2^bin_log2 pixels (the same for every view)
   int4* rec;                 // [4 * total_quads]: the 64-byte quad record (QuadRec)
   uint2* rec_rect;           // [total_quads]: pixel AABB (px0 | px1 << 16, py0 | py1 << 16)
   uint32_t* rec_info;        // [total_quads]: kInfo* bits | cull reason << 8
@@ -198,8 +208,8 @@ struct Ws {
   uint32_t* bin_order;       // [total_bins]: bins by decreasing reference count
   unsigned long long* refs;      // [refs_cap] sorted per bin: (~rep_bits << 32) | ~record
   unsigned long long* refs_tmp;  // [refs_cap] merge buffer of the high-density sort
-  uint32_t* ref_hb;          // [refs_cap + 32 * total_bins] per bin, the transposed half-block
-                             // bitmap of its sorted references (hb_row)
+  uint32_t* ref_hb;          // [mw * refs_cap + mrows * total_bins] per bin, the transposed
+                             // half-block bitmap of its sorted references (hb_row)
   uint32_t* ovf_list;        // [total_pix] flattened pixel ids registered for the exact path
   // backward
   const float* grad_out;     // f32[H][W][4] of view 0
@@ -225,11 +235,12 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
 }
 
 // The half-block bitmap of a bin with n sorted references starting at off: row h (one per
-// 8x4 half-block) holds nw = ceil(n / 32) words, bit j of word w set iff reference 32 w + j
-// overlaps half-block h. Rows of bin b start at off + 32 b, so the bitmaps of all bins fit
-// in refs + 32 * bins words.
+// 8x4 half-block; bin_mrows rows) holds nw = ceil(n / 32) words, bit j of word w set iff
+// reference 32 w + j overlaps half-block h. Rows of bin b start at mw * off + mrows * b, so
+// the bitmaps of all bins fit in mw * refs + mrows * bins words.
 __device__ __forceinline__ const uint32_t* hb_row(const Ws& ws, uint32_t off, int bin, int n, int hb) {
-  return ws.ref_hb + (size_t)off + 32 * (size_t)bin + (size_t)hb * (size_t)((n + 31) >> 5);
+  return ws.ref_hb + (size_t)bin_mw(ws.bin_log2) * off + (size_t)bin_mrows(ws.bin_log2) * (size_t)bin +
+         (size_t)hb * (size_t)((n + 31) >> 5);
 }
 
 // Position of the k-th (0-based) set bit of m; k < popc(m).

@@ -88,7 +88,8 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
 
   // ---- scratch layout (sizes must fit the static array) --------------------------------
   const long long Q = q.num_quads;
-  const int nbx = (width + kBin - 1) / kBin, nby = (height + kBin - 1) / kBin;
+  constexpr int kB = 1 << kBinLog2Default;   // 32-pixel bins, the default context's
+  const int nbx = (width + kB - 1) / kB, nby = (height + kB - 1) / kB;
   const long long nbins = (long long)nbx * nby, npix = (long long)width * height;
   size_t o = 0;
   const size_t o_ctrl = o; o = up256(o + sizeof(Ctrl));
@@ -189,6 +190,7 @@ extern "C" lr_status lr_render_noalloc(const lr_quads* quads, const lr_camera* c
   ws.total_quads = Q;
   ws.total_pix = npix;
   ws.refs_cap = cap;
+  ws.bin_log2 = kBinLog2Default;
   ws.rec = reinterpret_cast<int4*>(base + o_rec);
   ws.rec_rect = reinterpret_cast<uint2*>(base + o_rect);
   ws.rec_info = reinterpret_cast<uint32_t*>(base + o_info);

@@ -213,8 +213,9 @@ __device__ void overflow_pixel(const Ws& ws, long long pid, unsigned long long* 
   const ViewDev& V = ws.views[v];
   const long long pidx = pid - V.pix_base;
   const int px = (int)(pidx % V.width), py = (int)(pidx / V.width);
-  const int bin_g = V.bin_base + (py >> kBinLog2) * V.nbx + (px >> kBinLog2);
-  const int hb = ((py & (kBin - 1)) / kHbH) * (kBin / kHbW) + (px & (kBin - 1)) / kHbW;
+  const int lg = ws.bin_log2, B = 1 << lg;
+  const int bin_g = V.bin_base + (py >> lg) * V.nbx + (px >> lg);
+  const int hb = ((py & (B - 1)) / kHbH) * bin_hb_cols(lg) + (px & (B - 1)) / kHbW;
   const uint32_t off = ws.bin_off[bin_g];
   const int n = (int)(ws.bin_off[bin_g + 1] - off);
 

@@ -152,8 +152,8 @@ __global__ __launch_bounds__(256) void k_setup(Ws ws) {
           worst = kNoPixel;
         } else {
           rect = make_uint2((uint32_t)px0 | ((uint32_t)px1 << 16), (uint32_t)py0 | ((uint32_t)py1 << 16));
-          const int bw = (px1 >> kBinLog2) - (px0 >> kBinLog2) + 1;
-          const int bh = (py1 >> kBinLog2) - (py0 >> kBinLog2) + 1;
+          const int bw = (px1 >> ws.bin_log2) - (px0 >> ws.bin_log2) + 1;
+          const int bh = (py1 >> ws.bin_log2) - (py0 >> ws.bin_log2) + 1;
           if (bw > kSmallBins || bh > kSmallBins) info |= kInfoLarge;
           if (q[0] == q[1] && q[0] == q[2] && q[0] == q[3]) info |= kInfoFlatDepth;
           rep = rep_depth_of(X, Y, q, info, px0, px1, py0, py1);

@@ -1,4 +1,4 @@
-"""The autotuner times sorter capacities and CTA counts, requires every candidate's image
+"""The autotuner times sorter capacities, bin sizes and CTA counts, requires every candidate's image
 to agree within 1e-5 (the pipeline is exact for any K), and caches its choice."""
 import pytest
 
@@ -13,11 +13,14 @@ def test_autotune_small(tmp_path, monkeypatch):
     monkeypatch.setenv("LR_AUTOTUNE_CACHE", str(tmp_path / "cache.json"))
     s = scenegen.wavy_layers(320, 180, layers=16, nx=24, ny=12, seed=3)
     ds = P.DeviceScene.from_scene(s)
-    res = autotune.tune(ds, s.width, s.height, ks=(1, 2, 3, 8), ctas_per_sm=(0, 1), reps=2)
-    assert res["sorter_k"] in (1, 2, 3, 8)
-    assert len(res["table"]) == 8      # per-vertex colours: no colour-carrying variant
+    res = autotune.tune(ds, s.width, s.height, ks=(1, 2, 3, 8), ctas_per_sm=(0, 1), reps=2,
+                        bin_sizes=(16, 32, 64))
+    assert res["sorter_k"] in (1, 2, 3, 8) and res["bin_size"] in (16, 32, 64)
+    assert len(res["table"]) == 24     # per-vertex colours: no colour-carrying variant
+    assert {t["bin_size"] for t in res["table"]} == {16, 32, 64}
     # K = 1 cannot order interpenetrating layers by itself: more exact-path pixels
-    by_k = {t["sorter_k"]: t["overflow_pixels"] for t in res["table"] if t["raster_ctas_per_sm"] == 0}
+    by_k = {t["sorter_k"]: t["overflow_pixels"] for t in res["table"]
+            if t["raster_ctas_per_sm"] == 0 and t["bin_size"] == 32}
     assert by_k[1] >= by_k[8]
     again = autotune.tune(ds, s.width, s.height, ks=(1,), reps=1)
     assert again["sorter_k"] == res["sorter_k"]          # served from the cache
