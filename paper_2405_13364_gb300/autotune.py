@@ -74,10 +74,10 @@ def tune(scene, width: int, height: int, ks=DEFAULT_KS, ctas_per_sm=(0,), reps: 
     ref_img = None
     if carry is None:
         carry = (False, True) if scene.color_mode == 0 else (False,)
-    cands = [(k, c, cc, b) for b in bin_sizes for k in ks for c in ctas_per_sm for cc in carry]
-    for k, c, cc, b in cands:
+    cands = [(k, c, cc, bs) for bs in bin_sizes for k in ks for c in ctas_per_sm for cc in carry]
+    for k, c, cc, bs in cands:
         if True:
-            r = Renderer(sorter_k=k, raster_ctas_per_sm=c, device=device, carry_colors=cc, bin_size=b)
+            r = Renderer(sorter_k=k, raster_ctas_per_sm=c, device=device, carry_colors=cc, bin_size=bs)
             out = r.make_outputs(width, height)
             view = r.view_struct(scene, width, height, out)
             st = r.render_views([view])                    # sizes the workspace, checked
@@ -95,7 +95,7 @@ def tune(scene, width: int, height: int, ks=DEFAULT_KS, ctas_per_sm=(0,), reps: 
                 torch.cuda.synchronize()
                 times.append(a.elapsed_time(b))
             ovf = B_overflow(r)
-            table.append(dict(sorter_k=k, raster_ctas_per_sm=c, carry_colors=cc, bin_size=b,
+            table.append(dict(sorter_k=k, raster_ctas_per_sm=c, carry_colors=cc, bin_size=bs,
                               ms=statistics.median(times), overflow_pixels=ovf, fragments=int(st.fragments)))
             r.close()
     best = min(table, key=lambda t: t["ms"])
