@@ -787,26 +787,39 @@ def run_gpu(args):
 
 
 def run_profile(args):
-    """A short, self-contained run for ncu: a few frames of the benchmark workload, no
-    timing, no CPU baseline. Kernel launch order per frame: k_init, k_setup, k_bin_count,
-    k_bin_scan, k_bin_scatter, k_bin_sort, k_bin_sort_big, k_raster, k_overflow."""
+    """A short, self-contained run for ncu: a few frames of one workload, no timing, no CPU
+    baseline. --variant picks the rasteriser form: exact (the benchmark's), alpha (the
+    opt-in alpha threshold), lit (lit per-vertex colours on the layer scene) or msaa (4
+    samples per pixel, ending in k_resolve). Kernel launch order per exact frame: k_init,
+    k_setup, k_bin_count, k_bin_scan, k_bin_scatter, k_bin_sort, k_bin_sort_big, k_raster,
+    k_overflow."""
     import torch
 
     import paper_2405_13364_gb300 as P
     import scenegen
     torch.cuda.set_device(0)
-    scene = {"layers": scenegen.config_layers_1080p, "particles": scenegen.config_particles_1080p,
-             "frustum": scenegen.config_small_frustum, "diff": scenegen.config_diff_1024}[args.workload]()
-    r = P.Renderer(sorter_k=args.k)
+    if args.variant == "lit":
+        scene = scenegen.wavy_layers(color_mode=scenegen.COLOR_LIT)
+    else:
+        scene = {"layers": scenegen.config_layers_1080p, "particles": scenegen.config_particles_1080p,
+                 "frustum": scenegen.config_small_frustum, "diff": scenegen.config_diff_1024}[args.workload]()
+    r = P.Renderer(sorter_k=args.k, alpha_threshold=args.variant == "alpha")
+    if args.variant == "lit":
+        r.set_lighting(scene.light[:3], scene.light[3])
     ds = P.DeviceScene.from_scene(scene)
-    out = r.make_outputs(scene.width, scene.height)
-    view = r.view_struct(ds, scene.width, scene.height, out)
-    r.render_views([view])
-    for _ in range(args.steps):
-        r.render_views([view], check=False)
+    if args.variant == "msaa":
+        r.render_msaa(ds, scene.width, scene.height, samples=4)
+        for _ in range(args.steps):
+            r.render_msaa(ds, scene.width, scene.height, samples=4, check=False)
+    else:
+        out = r.make_outputs(scene.width, scene.height)
+        view = r.view_struct(ds, scene.width, scene.height, out)
+        r.render_views([view])
+        for _ in range(args.steps):
+            r.render_views([view], check=False)
     torch.cuda.synchronize()
     st = r.stats()
-    print(json.dumps({"profile_workload": args.workload, "frames": args.steps + 1,
+    print(json.dumps({"profile_workload": args.workload, "variant": args.variant, "frames": args.steps + 1,
                       "fragments": st["fragments"], "overflow_pixels": st["overflow_pixels"]}))
 
 
@@ -821,6 +834,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-particles", action="store_true", help="skip the particle-frame sub-object")
     ap.add_argument("--profile", action="store_true", help="short run for ncu (see run_profile)")
+    ap.add_argument("--variant", default="exact", choices=["exact", "alpha", "lit", "msaa"],
+                    help="rasteriser form of the --profile run")
     ap.add_argument("--workload", default="layers", choices=["layers", "particles", "frustum", "diff"])
     args = ap.parse_args()
     if args.profile:

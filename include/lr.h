@@ -189,10 +189,11 @@ typedef struct {
 /* Byte offsets, inside a workspace, of the per-quad records written by the setup stage and
  * of the binning arrays (for tests and inspection; valid after the render's stream has
  * finished and until the workspace is reused):
- *   rec       u32[Q][16] per quad: X0 Y0 X1 Y1 X2 Y2 X3 Y3 (snapped, 1/256 pixel), the
- *                        four vertices' 1/w (f32 bits), 1/|A0| and 1/|A1| (f32 bits of the
- *                        reciprocal doubled triangle areas, 0 for a zero-area triangle),
- *                        info (as rec_info), 0
+ *   rec       u32[Q][16] per visible quad (not written for a culled one): X0 Y0 X1 Y1 X2
+ *                        Y2 X3 Y3 (snapped, 1/256 pixel), the four vertices' 1/w (f32 bits),
+ *                        1/|A0| and 1/|A1| (f32 bits of the reciprocal doubled triangle
+ *                        areas, 0 for a zero-area triangle), info (as rec_info, cull reason
+ *                        0), 0
  *   rec_rect  u32[Q][2]  pixel-centre AABB: px0 | px1 << 16, py0 | py1 << 16
  *                        (0x0000FFFF, 0x0000FFFF for a culled quad)
  *   rec_info  u32[Q]     bit 0/1: triangle 0/1 has non-zero area, bit 2: spans more than

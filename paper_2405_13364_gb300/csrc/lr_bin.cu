@@ -193,7 +193,11 @@ __global__ __launch_bounds__(1024) void k_bin_scan(Ws ws) {
       nonempty += c > 0;
       high += c >= (uint32_t)kSortSmemCap;
       mx = c > mx ? c : mx;
-      atomicAdd(&cls_count[c ? 33 - __clz(c) : 0], 1u);
+      // one shared-memory atomic per warp and size class (most bins of a warp share one)
+      const uint32_t cls = c ? 33 - __clz(c) : 0;
+      const unsigned act = __activemask();
+      const unsigned peers = __match_any_sync(act, cls);
+      if (lane == __ffs(peers) - 1) atomicAdd(&cls_count[cls], (uint32_t)__popc(peers));
     }
     unsigned long long x = c;
 #pragma unroll
@@ -250,8 +254,15 @@ __global__ __launch_bounds__(1024) void k_bin_scan(Ws ws) {
   __syncthreads();
   for (int i = tid; i < n; i += 1024) {
     const uint32_t c = ws.bin_count[i];
-    const uint32_t pos = atomicAdd(&cls_base[c ? 33 - __clz(c) : 0], 1u);
-    ws.bin_order[pos] = (uint32_t)i;
+    const uint32_t cls = c ? 33 - __clz(c) : 0;
+    // lanes of one class take consecutive positions from one atomic of their leader
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, cls);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&cls_base[cls], (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    ws.bin_order[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
   }
 }
 

@@ -24,10 +24,13 @@ constexpr int kTileLog2 = 5;                // 32x32-pixel tiles of lr_view.owne
 // per row and rows, numbered hy * cols + hx; the transposed half-block bitmap of a bin
 // keeps mrows >= 32 rows (a multiple of 32, so that a reference's half-block mask is mw
 // whole 32-bit words).
-__host__ __device__ __forceinline__ int bin_hb(int lg) { return 1 << (2 * lg - 5); }        // 8, 32, 128
-__host__ __device__ __forceinline__ int bin_hb_cols(int lg) { return 1 << (lg - 3); }       // 2, 4, 8
-__host__ __device__ __forceinline__ int bin_mrows(int lg) { return bin_hb(lg) < 32 ? 32 : bin_hb(lg); }
-__host__ __device__ __forceinline__ int bin_mw(int lg) { return bin_mrows(lg) >> 5; }       // 1, 1, 4
+__host__ __device__ __forceinline__ int bin_hb_log2(int lg) { return 2 * lg - 5; }            // 3, 5, 7
+__host__ __device__ __forceinline__ int bin_hb(int lg) { return 1 << bin_hb_log2(lg); }       // 8, 32, 128
+__host__ __device__ __forceinline__ int bin_hb_cols_log2(int lg) { return lg - 3; }           // 1, 2, 3
+__host__ __device__ __forceinline__ int bin_hb_cols(int lg) { return 1 << (lg - 3); }         // 2, 4, 8
+__host__ __device__ __forceinline__ int bin_mrows_log2(int lg) { return lg < 5 ? 5 : 2 * lg - 5; }
+__host__ __device__ __forceinline__ int bin_mrows(int lg) { return 1 << bin_mrows_log2(lg); }  // 32, 32, 128
+__host__ __device__ __forceinline__ int bin_mw(int lg) { return bin_mrows(lg) >> 5; }         // 1, 1, 4
 constexpr float kGuardPx = 16384.0f;        // guard band, pixels
 constexpr int kSortSmemCap = 2048;          // bins below this many refs: k_bin_sort (256 threads)
 constexpr int kSortBigCap = 8192;           // k_bin_sort_big sorts runs of up to this many refs
@@ -239,8 +242,8 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
 // reference 32 w + j overlaps half-block h. Rows of bin b start at mw * off + mrows * b, so
 // the bitmaps of all bins fit in mw * refs + mrows * bins words.
 __device__ __forceinline__ const uint32_t* hb_row(const Ws& ws, uint32_t off, int bin, int n, int hb) {
-  return ws.ref_hb + (size_t)bin_mw(ws.bin_log2) * off + (size_t)bin_mrows(ws.bin_log2) * (size_t)bin +
-         (size_t)hb * (size_t)((n + 31) >> 5);
+  const int ml = bin_mrows_log2(ws.bin_log2);
+  return ws.ref_hb + ((size_t)off << (ml - 5)) + ((size_t)bin << ml) + (size_t)hb * (size_t)((n + 31) >> 5);
 }
 
 // Position of the k-th (0-based) set bit of m; k < popc(m).

@@ -466,14 +466,14 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
     if (lane == 0) item = atomicAdd(&ws.ctrl->raster_head, 1ull);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= nitems) break;
-    const int lg = ws.bin_log2, hbn = bin_hb(lg), cols = bin_hb_cols(lg);
-    const int bin_g = (int)ws.bin_order[item / hbn];
-    const int hb = (int)(item % hbn);
+    const int lg = ws.bin_log2, hl = bin_hb_log2(lg), cl = bin_hb_cols_log2(lg);
+    const int bin_g = (int)ws.bin_order[item >> hl];
+    const int hb = (int)(item & ((1u << hl) - 1u));
     const int v = view_of_bin(ws.views, ws.n_views, bin_g);
     const ViewDev& V = ws.views[v];
     const int b = bin_g - V.bin_base;
     const int bx = b % V.nbx, by = b / V.nbx;
-    const int ox = (bx << lg) + (hb % cols) * kHbW, oy = (by << lg) + (hb / cols) * kHbH;
+    const int ox = (bx << lg) + (hb & ((1 << cl) - 1)) * kHbW, oy = (by << lg) + (hb >> cl) * kHbH;
     if (ox >= V.width || oy >= V.height || !tile_owned(V, ox, oy)) continue;
     const int px = ox + lx, py = oy + ly;
     const bool pix_ok = px < V.width && py < V.height;

@@ -136,9 +136,12 @@ __global__ __launch_bounds__(256) void k_setup(Ws ws) {
           const float it = __frcp_rn(__ll2float_rn(A));
           if (t) inv.y = it; else inv.x = it;
           const int xb = t ? X[2] : X[1], yb = t ? Y[2] : Y[1], xc = t ? X[3] : X[2], yc = t ? Y[3] : Y[2];
-          const long long wx = (long long)max(X[0], max(xb, xc)) - min(X[0], min(xb, xc));
-          const long long wy = (long long)max(Y[0], max(yb, yc)) - min(Y[0], min(yb, yc));
-          if (wx * (wy + 3 * 256) + wy * (wx + 7 * 256) + 1 < (1LL << 30)) info |= kInfoSmall0 << t;
+          // (vertex boxes lie within the guard band, so the extents fit 32 bits; below 2^15
+          // each the bound's two products and their sum fit an unsigned 32-bit word)
+          const uint32_t wx = (uint32_t)(max(X[0], max(xb, xc)) - min(X[0], min(xb, xc)));
+          const uint32_t wy = (uint32_t)(max(Y[0], max(yb, yc)) - min(Y[0], min(yb, yc)));
+          if (wx < 32768u && wy < 32768u && wx * (wy + 3u * 256u) + wy * (wx + 7u * 256u) + 1u < (1u << 30))
+            info |= kInfoSmall0 << t;
         }
         const int xmin = min(min(X[0], X[1]), min(X[2], X[3]));
         const int xmax = max(max(X[0], X[1]), max(X[2], X[3]));
@@ -165,14 +168,18 @@ __global__ __launch_bounds__(256) void k_setup(Ws ws) {
       rect = make_uint2(kRectInvisible, kRectInvisible);
     }
     reason = worst;
-    int4* rp = ws.rec + 4 * g;
-    rp[0] = make_int4(X[0], Y[0], X[1], Y[1]);
-    rp[1] = make_int4(X[2], Y[2], X[3], Y[3]);
-    rp[2] = make_int4(__float_as_int(q[0]), __float_as_int(q[1]), __float_as_int(q[2]), __float_as_int(q[3]));
-    rp[3] = make_int4(__float_as_int(inv.x), __float_as_int(inv.y), (int)(info | (worst << 8)), 0);
+    // later stages read the record and the representative depth of visible quads only (a
+    // culled quad's invisible rectangle keeps it out of every bin), so culled quads skip them
+    if (worst == kVisible) {
+      int4* rp = ws.rec + 4 * g;
+      rp[0] = make_int4(X[0], Y[0], X[1], Y[1]);
+      rp[1] = make_int4(X[2], Y[2], X[3], Y[3]);
+      rp[2] = make_int4(__float_as_int(q[0]), __float_as_int(q[1]), __float_as_int(q[2]), __float_as_int(q[3]));
+      rp[3] = make_int4(__float_as_int(inv.x), __float_as_int(inv.y), (int)info, 0);
+      ws.rec_rep[g] = rep;
+    }
     ws.rec_rect[g] = rect;
     ws.rec_info[g] = info | (worst << 8);
-    ws.rec_rep[g] = rep;
     if (bad) set_error(ws.ctrl, LR_ERR_INVALID_ARG);
   }
   // statistics: culled quads per reason, one atomic per reason present in the warp (the
