@@ -45,8 +45,15 @@ LAUNCHES_PER_FRAME = 9
 RASTER_TRAFFIC = {
     # (DRAM read + write bytes per launch, ncu smsp__issue_active, ncu smsp__inst_executed,
     #  source hash of the captured build)
-    ("layers", 1, False): (102_125_056, 0.786, 392_622_816, "a5f3cc2466cfb7ff"),      # profiles/k_raster_layers1080p.md
-    ("particles", 1, False): (382_462_976, 0.709, 906_694_001, "a5f3cc2466cfb7ff"),  # profiles/k_raster_particles1080p.md
+    ("layers", 1, False): (101_949_952, 0.785, 397_258_354, "cb89960c97d0703f"),      # profiles/k_raster_layers1080p.md
+    ("particles", 1, False): (382_221_056, 0.7059, 909_416_664, "cb89960c97d0703f"),  # profiles/k_raster_particles1080p.md
+}
+# the same for the rasteriser's variants and the multisample resolve on the layer frame
+# (K = 1): (DRAM bytes per launch, issue-slot share, warp instructions, kernel us, hash)
+VARIANT_CAPTURES = {
+    "alpha_threshold": (93_722_624, 0.7402, 288_854_926, 318.1, "cb89960c97d0703f"),   # profiles/k_raster_alpha_layers1080p.md
+    "lit": (116_462_080, 0.5867, 461_388_581, 632.6, "cb89960c97d0703f"),               # profiles/k_raster_lit_layers1080p.md
+    "msaa_resolve": (149_178_615, 0.2648, 7_452_000, 26.8, "cb89960c97d0703f"),         # profiles/k_resolve_msaa4_layers1080p.md
 }
 RASTER_SOURCES = ("lr_raster.cuh", "lr_common.cuh")
 LANES_PER_SM_CLK = 128
@@ -110,11 +117,22 @@ def raster_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def raster_capture(workload: str, k: int, carry: bool):
+def variant_capture(name: str):
+    """The committed ncu figures of a rasteriser variant (or the resolve) as a dict, or None
+    once the rasteriser's sources differ from the captured build."""
+    t = VARIANT_CAPTURES.get(name)
+    if t is None or t[4] != raster_source_hash():
+        return None
+    return {"dram_bytes_per_launch": t[0], "issue_active": t[1], "warp_instructions": t[2], "kernel_us": t[3],
+            "source": "ncu capture, K = 1, layers-1080p frame (profiles/)"}
+
+
+def raster_capture(workload: str, k: int, carry: bool, bin_size: int = 32):
     """(traffic bytes, issue-slot utilisation, warp instructions) of the committed ncu
-    capture of this rasteriser build, or Nones once the sources differ from it."""
+    capture of this rasteriser build (taken with 32-pixel bins), or Nones once the sources
+    differ from it or the configuration is another."""
     t = RASTER_TRAFFIC.get((workload, k, carry))
-    if t is None or t[3] != raster_source_hash():
+    if t is None or t[3] != raster_source_hash() or bin_size != 32:
         return None, None, None
     return t[0], t[1], t[2]
 
@@ -223,7 +241,7 @@ def frame_benchmark(P, torch, scene, k, carry, steps, warmup, flush, dev, dist=N
     return sum(ms) / len(ms), st0, stages, sampler, (r, ds, out, view)
 
 
-def raster_roofline(workload, k, carry, frags, raster_ms, sm_count, sm_max_mhz):
+def raster_roofline(workload, k, carry, frags, raster_ms, sm_count, sm_max_mhz, bin_size=32):
     """The rasteriser against the plain-ALU peak: algorithmic lane operations per fragment
     (25 + K) x fragments / its CUDA-event time, against SMs x 128 lanes x the SM clock,
     with the SM count of the device the run is on; plus the instruction-issue ceiling of
@@ -231,7 +249,7 @@ def raster_roofline(workload, k, carry, frags, raster_ms, sm_count, sm_max_mhz):
     ops = (OPS_PER_FRAG_BASE + k) * frags
     peak = sm_count * LANES_PER_SM_CLK * sm_max_mhz * 1e6 / 1e12   # T lane-ops/s
     achieved = ops / (raster_ms * 1e-3) / 1e12
-    traffic, issue_active, inst = raster_capture(workload, k, carry)
+    traffic, issue_active, inst = raster_capture(workload, k, carry, bin_size)
     issue_ceiling = None
     if inst:
         ceil_gfrag = sm_count * 4 * sm_max_mhz * 1e6 / (inst / frags) / 1e9
@@ -273,7 +291,7 @@ def particles_benchmark(P, torch, args, flush, dev, sm_count, hbm_gbs):
             "stage_ms": stages, "overflow_pixels": st0["overflow_pixels"], "bins_high": st0["bins_high"],
             "sort_bins": st0["sort_bins"],
             "roofline": raster_roofline("particles", k, carry, frags, stages["raster"], sm_count,
-                                        clocks.get("sm_max_mhz") or 2070.0),
+                                        clocks.get("sm_max_mhz") or 2070.0, tuned["bin_size"]),
             **stage_rooflines(scene, st0, stages, hbm_gbs), "clocks": clocks}
 
 
@@ -626,7 +644,7 @@ def run_gpu(args):
     clocks = sampler.summary()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     roofline = raster_roofline(args.workload, args.k, carry, frags, stages["raster"], sm_count,
-                               clocks.get("sm_max_mhz") or 2070.0)
+                               clocks.get("sm_max_mhz") or 2070.0, bin_size)
     peaks = _measured_peaks()
     hbm = peaks.get("hbm_gbs") if peaks else None
     particles = None
@@ -671,7 +689,8 @@ def run_gpu(args):
                            "speedup_vs_exact": round(ms_step / a_ms, 3),
                            "fragments_evaluated": int(sta["fragments"]), "fragments_exact": frags,
                            "overflow_pixels": int(sta["overflow_pixels"]),
-                           "max_abs_deviation_from_exact": round(dev_max, 6), "bound": 1 / 128}
+                           "max_abs_deviation_from_exact": round(dev_max, 6), "bound": 1 / 128,
+                           "ncu": variant_capture("alpha_threshold")}
         ra.close()
 
     # ---- multisampling (4 samples per pixel, every sample an exact composite) ------------
@@ -695,7 +714,7 @@ def run_gpu(args):
         msaa = {"samples": 4, "ms_per_frame": round(m_ms, 4),
                 "sample_fragments_per_frame": int(stm["fragments"]),
                 "gfrag_s": round(int(stm["fragments"]) / (m_ms * 1e-3) / 1e9, 2),
-                "vs_single_sample_ms": round(m_ms / ms_step, 3)}
+                "vs_single_sample_ms": round(m_ms / ms_step, 3), "ncu_resolve": variant_capture("msaa_resolve")}
         rm.close()
 
     # ---- lit colours (per-vertex normals, one directional light) on the same layers ------
@@ -722,7 +741,8 @@ def run_gpu(args):
         l_ms = sum(a0.elapsed_time(a1) for a0, a1 in l_ev) / len(l_ev)
         lit = {"ms_per_frame": round(l_ms, 4), "gfrag_s": round(frags / (l_ms * 1e-3) / 1e9, 2),
                "vs_unlit_ms": round(l_ms / ms_step, 3),
-               "shading": "per fragment: perspective-correct normal, two-sided Lambert + ambient"}
+               "shading": "per fragment: perspective-correct normal, two-sided Lambert + ambient",
+               "ncu": variant_capture("lit")}
         rl.close()
         del lds
 
