@@ -96,6 +96,12 @@ typedef struct {
                                 and 16 for dense regions); default 32. Any bin size gives the
                                 same exact image: it changes how many (quad, bin) references
                                 binning makes and how large the per-bin depth sorts are. */
+  int32_t block_h;           /* rows of the rasteriser's work item: 4 (8x4 half-blocks, the
+                                default) or 8 (8x8 blocks, Sec. 2, Stage 3, Phase 2: a quad
+                                meeting both halves is set up once). 8 applies to forward
+                                exact renders with flat or per-vertex colours and sorter_k
+                                1, 2 or 3; other renders of the context use 8x4. The image
+                                is the same either way. */
 } lr_config;
 
 /* A quad scene (Sec. 2: quads, not triangles, are the input primitive). Device memory. */

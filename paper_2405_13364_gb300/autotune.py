@@ -1,13 +1,14 @@
 """Autotuner for the rasteriser's launch parameters.
 
 Tunable here: the per-pixel sorter capacity K (the paper's depth-filter size, Sec. 2
-"Sample blending"), the bin size of the binning stage (16, 32 or 64 pixels; Sec. 2, Stage 2
+"Sample blending"), the rasteriser's work item (8x4 half-blocks or 8x8 blocks, Sec. 2,
+Stage 3), the bin size of the binning stage (16, 32 or 64 pixels; Sec. 2, Stage 2
 uses 32 and Sec. 4 proposes 64 and 16 for sparse and dense regions), the number of
 persistent rasteriser CTAs per SM, and for flat-colour scenes whether the sorter carries
 colours. Every candidate gives the same coverage and the same exact fragment order; K only
 moves pixels between the sorter and the exact overflow path, whose composite sums in a
 different order, so colours agree to fp32 rounding (the tuner checks 1e-5, the accuracy
-bar) rather than bit for bit. The half-block shape (8x4) is fixed.
+bar) rather than bit for bit. The work item is an 8x4 half-block or an 8x8 block.
 
 The tuner renders the workload with every candidate, checks that all candidates produce
 the same image within 1e-5, times each with CUDA events (median of `reps`), and caches the
@@ -61,10 +62,12 @@ def lookup(width, height, num_quads, color_mode, device=None):
 
 
 def tune(scene, width: int, height: int, ks=DEFAULT_KS, ctas_per_sm=(0,), reps: int = 5,
-         use_cache: bool = True, device=None, carry=None, bin_sizes=(32,)):
+         use_cache: bool = True, device=None, carry=None, bin_sizes=(32,), block_hs=(4,)):
     """scene: a DeviceScene. Returns {'sorter_k', 'raster_ctas_per_sm', 'carry_colors',
-    'bin_size', 'ms', 'table'}. carry: candidates for carrying flat colours in the sorter
-    (default: both for flat-colour scenes). bin_sizes: candidate bin sizes (16, 32, 64)."""
+    'bin_size', 'block_h', 'ms', 'table'}. carry: candidates for carrying flat colours in the
+    sorter (default: both for flat-colour scenes). bin_sizes: candidate bin sizes (16, 32,
+    64). block_hs: candidate work-item heights (4: 8x4 half-blocks, 8: 8x8 blocks, built
+    for sorter capacities up to 3)."""
     from . import Renderer
     key = workload_key(width, height, scene.num_quads, scene.color_mode, device)
     cache = _load_cache() if use_cache else {}
@@ -74,10 +77,12 @@ def tune(scene, width: int, height: int, ks=DEFAULT_KS, ctas_per_sm=(0,), reps: 
     ref_img = None
     if carry is None:
         carry = (False, True) if scene.color_mode == 0 else (False,)
-    cands = [(k, c, cc, bs) for bs in bin_sizes for k in ks for c in ctas_per_sm for cc in carry]
-    for k, c, cc, bs in cands:
+    cands = [(k, c, cc, bs, bh) for bh in block_hs for bs in bin_sizes for k in ks for c in ctas_per_sm
+             for cc in carry if bh == 4 or k <= 3]
+    for k, c, cc, bs, bh in cands:
         if True:
-            r = Renderer(sorter_k=k, raster_ctas_per_sm=c, device=device, carry_colors=cc, bin_size=bs)
+            r = Renderer(sorter_k=k, raster_ctas_per_sm=c, device=device, carry_colors=cc, bin_size=bs,
+                         block_h=bh)
             out = r.make_outputs(width, height)
             view = r.view_struct(scene, width, height, out)
             st = r.render_views([view])                    # sizes the workspace, checked
@@ -95,12 +100,13 @@ def tune(scene, width: int, height: int, ks=DEFAULT_KS, ctas_per_sm=(0,), reps: 
                 torch.cuda.synchronize()
                 times.append(a.elapsed_time(b))
             ovf = B_overflow(r)
-            table.append(dict(sorter_k=k, raster_ctas_per_sm=c, carry_colors=cc, bin_size=bs,
+            table.append(dict(sorter_k=k, raster_ctas_per_sm=c, carry_colors=cc, bin_size=bs, block_h=bh,
                               ms=statistics.median(times), overflow_pixels=ovf, fragments=int(st.fragments)))
             r.close()
     best = min(table, key=lambda t: t["ms"])
     result = dict(sorter_k=best["sorter_k"], raster_ctas_per_sm=best["raster_ctas_per_sm"],
-                  carry_colors=best["carry_colors"], bin_size=best["bin_size"], ms=best["ms"], table=table)
+                  carry_colors=best["carry_colors"], bin_size=best["bin_size"], block_h=best["block_h"],
+                  ms=best["ms"], table=table)
     if use_cache:
         cache[key] = result
         _save_cache(cache)

@@ -46,6 +46,12 @@ LR_DECLARE_RASTER(4)
 LR_DECLARE_RASTER(6)
 LR_DECLARE_RASTER(8)
 LR_DECLARE_RASTER(12)
+#define LR_DECLARE_RASTER8(KK)                                                                    \
+  cudaError_t prepare_raster8_##KK(int* blocks_flat, int* blocks_vtx);                            \
+  cudaError_t launch_raster8_##KK(int mode, const Ws& ws, int grid, cudaStream_t st);
+LR_DECLARE_RASTER8(1)
+LR_DECLARE_RASTER8(2)
+LR_DECLARE_RASTER8(3)
 
 __global__ void k_write_views(ViewChunk chunk, ViewDev* dst) {
   pdl_begin();
@@ -55,18 +61,26 @@ __global__ void k_write_views(ViewChunk chunk, ViewDev* dst) {
 
 typedef cudaError_t (*PrepareFn)(int*, int*, int*, int*);
 typedef cudaError_t (*LaunchFn)(int, const Ws&, int, cudaStream_t);   // mode 0 flat, 1 colours, 2 backward
+typedef cudaError_t (*Prepare8Fn)(int*, int*);
 
+// A sorter capacity's rasterisers: 8x4 half-blocks (every mode) and, for K <= 3, 8x8 blocks
+// (forward exact renders, flat or carried colours, with or without the coverage hash).
 struct RasterVariant {
   int k;
   PrepareFn prepare;
   LaunchFn launch;
+  Prepare8Fn prepare8;
+  LaunchFn launch8;
 };
 
 static const RasterVariant kVariants[] = {
-    {1, prepare_raster_1, launch_raster_1},   {2, prepare_raster_2, launch_raster_2},
-    {3, prepare_raster_3, launch_raster_3},   {4, prepare_raster_4, launch_raster_4},
-    {6, prepare_raster_6, launch_raster_6},   {8, prepare_raster_8, launch_raster_8},
-    {12, prepare_raster_12, launch_raster_12},
+    {1, prepare_raster_1, launch_raster_1, prepare_raster8_1, launch_raster8_1},
+    {2, prepare_raster_2, launch_raster_2, prepare_raster8_2, launch_raster8_2},
+    {3, prepare_raster_3, launch_raster_3, prepare_raster8_3, launch_raster8_3},
+    {4, prepare_raster_4, launch_raster_4, nullptr, nullptr},
+    {6, prepare_raster_6, launch_raster_6, nullptr, nullptr},
+    {8, prepare_raster_8, launch_raster_8, nullptr, nullptr},
+    {12, prepare_raster_12, launch_raster_12, nullptr, nullptr},
 };
 
 struct Layout {
@@ -178,6 +192,7 @@ using namespace lr;
 struct VariantState {
   const RasterVariant* v = nullptr;
   int flat = 1, vtx = 1, bwd = 1, lit = 1;
+  int flat8 = 1, vtx8 = 1;     // the 8x8-block kernels (when the capacity has them)
 };
 
 struct lr_ctx {
@@ -231,8 +246,10 @@ extern "C" lr_status lr_create(const lr_config* config, lr_ctx** out_ctx) {
   if (g.sorter_k <= 0) g.sorter_k = 3;
   if (g.ref_factor <= 0) g.ref_factor = 4;
   if (g.bin_size <= 0) g.bin_size = 1 << kBinLog2Default;
+  if (g.block_h <= 0) g.block_h = kHbH;
   c->bin_log2 = g.bin_size == 16 ? 4 : (g.bin_size == 32 ? 5 : (g.bin_size == 64 ? 6 : -1));
-  if (g.max_width > 65535 || g.max_height > 65535 || g.raster_ctas_per_sm < 0 || c->bin_log2 < 0) {
+  if (g.max_width > 65535 || g.max_height > 65535 || g.raster_ctas_per_sm < 0 || c->bin_log2 < 0 ||
+      (g.block_h != 4 && g.block_h != 8)) {
     delete c;
     return LR_ERR_INVALID_ARG;
   }
@@ -255,16 +272,12 @@ extern "C" lr_status lr_create(const lr_config* config, lr_ctx** out_ctx) {
     VariantState& V = c->vs[i];
     V.v = &kVariants[i];
     e = V.v->prepare(&V.flat, &V.vtx, &V.bwd, &V.lit);
-    if (g.raster_ctas_per_sm > 0) {
-      V.flat = std::min(V.flat, g.raster_ctas_per_sm);
-      V.vtx = std::min(V.vtx, g.raster_ctas_per_sm);
-      V.bwd = std::min(V.bwd, g.raster_ctas_per_sm);
-      V.lit = std::min(V.lit, g.raster_ctas_per_sm);
+    if (e == cudaSuccess && V.v->prepare8 && g.block_h == 8) e = V.v->prepare8(&V.flat8, &V.vtx8);
+    int* all[] = {&V.flat, &V.vtx, &V.bwd, &V.lit, &V.flat8, &V.vtx8};
+    for (int* x : all) {
+      if (g.raster_ctas_per_sm > 0) *x = std::min(*x, g.raster_ctas_per_sm);
+      *x = std::max(*x, 1);
     }
-    V.flat = std::max(V.flat, 1);
-    V.vtx = std::max(V.vtx, 1);
-    V.bwd = std::max(V.bwd, 1);
-    V.lit = std::max(V.lit, 1);
   }
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bin_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)kSortSmemBytes);
@@ -566,8 +579,15 @@ static lr_status launch_sequence(lr_ctx* ctx, const Prepared& P, cudaStream_t st
   const int mode = bwd ? 2 : (P.any_lit ? 17 : ((carry ? 1 : 0) | (P.any_hash ? 4 : 0) | (ath ? 8 : 0)));
   ws.t_min = ath ? kAlphaTMin : 0.0f;
   const VariantState& VS = ctx->vs[P.variant];
-  const int rblocks = bwd ? VS.bwd : (P.any_lit ? VS.lit : (carry ? VS.vtx : VS.flat));
-  cudaError_t e = VS.v->launch(mode, ws, ctx->sms * rblocks, st);
+  // 8x8 blocks for forward exact renders of flat or carried colours, when asked for and built
+  const bool blk8 = ctx->cfg.block_h == 8 && VS.v->launch8 && !bwd && !ath && !P.any_lit;
+  cudaError_t e;
+  if (blk8) {
+    e = VS.v->launch8(mode, ws, ctx->sms * (carry ? VS.vtx8 : VS.flat8), st);
+  } else {
+    const int rblocks = bwd ? VS.bwd : (P.any_lit ? VS.lit : (carry ? VS.vtx : VS.flat));
+    e = VS.v->launch(mode, ws, ctx->sms * rblocks, st);
+  }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "raster launch");
   rec(ctx, timed, 6, st);
   e = launch_overflow(bwd != nullptr, ws, ctx->sms * ctx->ovf_blocks, st, pdl);

@@ -97,7 +97,9 @@ __device__ __forceinline__ void edges64(const TriSm& T, int px, int py, long lon
 }
 
 // Builds the per-half-block record of triangle t of a quad; returns false if the triangle
-// has zero area or its pixel AABB misses the half-block.
+// has zero area or its pixel AABB misses the half-block (BH rows: 4, or 8 for the 8x8
+// blocks of k_raster8).
+template <int BH = kHbH>
 static __device__ __noinline__ bool setup_tri(TriSm& T, const int X[4], const int Y[4], const float qv[4],
                                           uint32_t info, int t, uint32_t jl, int ox, int oy,
                                           int cor[3], int box[4], int le[3], int lsx[3], int lsy[3]) {
@@ -120,11 +122,11 @@ static __device__ __noinline__ bool setup_tri(TriSm& T, const int X[4], const in
   const int ymin = min(ya, min(yb, yc)), ymax = max(ya, max(yb, yc));
   const int bx0 = ceil_div256((long long)xmin - 128), bx1 = floor_div256((long long)xmax - 128);
   const int by0 = ceil_div256((long long)ymin - 128), by1 = floor_div256((long long)ymax - 128);
-  if (bx0 > ox + kHbW - 1 || bx1 < ox || by0 > oy + kHbH - 1 || by1 < oy) return false;
+  if (bx0 > ox + kHbW - 1 || bx1 < ox || by0 > oy + BH - 1 || by1 < oy) return false;
   box[0] = max(bx0 - ox, 0);
   box[1] = min(bx1 - ox, kHbW - 1);
   box[2] = max(by0 - oy, 0);
-  box[3] = min(by1 - oy, kHbH - 1);
+  box[3] = min(by1 - oy, BH - 1);
   cor[0] = 0; cor[1] = ib; cor[2] = ic;
   T.X[0] = xa; T.X[1] = xb; T.X[2] = xc;
   T.Y[0] = ya; T.Y[1] = yb; T.Y[2] = yc;
@@ -141,7 +143,7 @@ static __device__ __noinline__ bool setup_tri(TriSm& T, const int X[4], const in
     const bool owned = dy < 0 || (dy == 0 && dx > 0);
     const long long e0 = dx * (P0y - uy[k]) - dy * (P0x - ux[k]) + (owned ? 0 : -1);
     const long long sx = -256 * dy, sy = 256 * dx;
-    const long long c1 = e0 + (kHbW - 1) * sx, c2 = e0 + (kHbH - 1) * sy, c3 = c1 + (kHbH - 1) * sy;
+    const long long c1 = e0 + (kHbW - 1) * sx, c2 = e0 + (BH - 1) * sy, c3 = c1 + (BH - 1) * sy;
     fast &= (e0 > -lim && e0 < lim && c1 > -lim && c1 < lim && c2 > -lim && c2 < lim && c3 > -lim && c3 < lim);
     le[k] = (int)e0;
     lsx[k] = (int)sx;
@@ -157,8 +159,10 @@ static __device__ __noinline__ bool setup_tri(TriSm& T, const int X[4], const in
 }
 
 // setup_tri for a triangle that k_setup marked small (kInfoSmall0 << t): the orientation
-// and 1/area come precomputed, and every edge value on a half-block the triangle's box
-// touches fits in 32 bits, so the whole set-up is 32-bit integer arithmetic.
+// and 1/area come precomputed, and every edge value at the pixel centres of the box's rows,
+// up to 7 pixels to either side of the box, fits in 32 bits, so the whole set-up is 32-bit
+// integer arithmetic (a block row outside the box is masked off, whatever its values).
+template <int BH = kHbH>
 __device__ __forceinline__ bool setup_tri_small(TriSm& T, const int X[4], const int Y[4], const float qv[4],
                                                 float inv, uint32_t info, int t, uint32_t jl, int ox, int oy,
                                                 int cor[3], int box[4], int le[3], int lsx[3], int lsy[3]) {
@@ -177,11 +181,11 @@ __device__ __forceinline__ bool setup_tri_small(TriSm& T, const int X[4], const 
   // pixel-centre box: ceil((min - 128) / 256) .. floor((max - 128) / 256)
   const int bx0 = (min(xa, min(xb, xc)) + 127) >> 8, bx1 = (max(xa, max(xb, xc)) - 128) >> 8;
   const int by0 = (min(ya, min(yb, yc)) + 127) >> 8, by1 = (max(ya, max(yb, yc)) - 128) >> 8;
-  if (bx0 > ox + kHbW - 1 || bx1 < ox || by0 > oy + kHbH - 1 || by1 < oy) return false;
+  if (bx0 > ox + kHbW - 1 || bx1 < ox || by0 > oy + BH - 1 || by1 < oy) return false;
   box[0] = max(bx0 - ox, 0);
   box[1] = min(bx1 - ox, kHbW - 1);
   box[2] = max(by0 - oy, 0);
-  box[3] = min(by1 - oy, kHbH - 1);
+  box[3] = min(by1 - oy, BH - 1);
   cor[0] = 0; cor[1] = ib; cor[2] = ic;
   T.kq = make_float4(qa, __fsub_rn(qb, qa), __fsub_rn(qc, qa), inv);
   uint32_t flags = kTriValid | kTriFast | ((qb == qa && qc == qa) ? kTriConstKey : 0u);
