@@ -33,17 +33,35 @@ __device__ __forceinline__ bool frag_eval_r(const Ws& ws, const ViewDev& V, cons
   const int yb = ib == 1 ? R.Y[1] : (ib == 2 ? R.Y[2] : R.Y[3]);
   const int xc = ic == 1 ? R.X[1] : (ic == 2 ? R.X[2] : R.X[3]);
   const int yc = ic == 1 ? R.Y[1] : (ic == 2 ? R.Y[2] : R.Y[3]);
-  const long long Px = 256LL * px + 128, Py = 256LL * py + 128;
-  // edge functions e0 = E(b -> c), e1 = E(c -> a), e2 = E(a -> b); top-left rule
+  // edge functions e0 = E(b -> c), e1 = E(c -> a), e2 = E(a -> b); top-left rule. A
+  // covered pixel centre lies inside the triangle's vertex box, so a pixel outside the
+  // triangle's pixel-centre box is not covered; inside it, a triangle k_setup marked small
+  // has every edge value in (-2^30, 2^30), and 32-bit arithmetic is exact. Otherwise 64-bit.
   long long e[3];
   {
     const int ux[3] = {xb, xc, xa}, uy[3] = {yb, yc, ya}, wx[3] = {xc, xa, xb}, wy[3] = {yc, ya, yb};
+    if (R.info & (kInfoSmall0 << t)) {
+      if (px < ((min(xa, min(xb, xc)) + 127) >> 8) || px > ((max(xa, max(xb, xc)) - 128) >> 8) ||
+          py < ((min(ya, min(yb, yc)) + 127) >> 8) || py > ((max(ya, max(yb, yc)) - 128) >> 8))
+        return false;
+      const int Px = 256 * px + 128, Py = 256 * py + 128;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const long long dx = (long long)wx[k] - ux[k], dy = (long long)wy[k] - uy[k];
-      e[k] = dx * (Py - uy[k]) - dy * (Px - ux[k]);
-      const bool owned = dy < 0 || (dy == 0 && dx > 0);
-      if (!(e[k] > 0 || (e[k] == 0 && owned))) return false;
+      for (int k = 0; k < 3; ++k) {
+        const int dx = wx[k] - ux[k], dy = wy[k] - uy[k];
+        const int ek = (int)((uint32_t)dx * (uint32_t)(Py - uy[k]) - (uint32_t)dy * (uint32_t)(Px - ux[k]));
+        e[k] = ek;
+        const bool owned = dy < 0 || (dy == 0 && dx > 0);
+        if (!(ek > 0 || (ek == 0 && owned))) return false;
+      }
+    } else {
+      const long long Px = 256LL * px + 128, Py = 256LL * py + 128;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const long long dx = (long long)wx[k] - ux[k], dy = (long long)wy[k] - uy[k];
+        e[k] = dx * (Py - uy[k]) - dy * (Px - ux[k]);
+        const bool owned = dy < 0 || (dy == 0 && dx > 0);
+        if (!(e[k] > 0 || (e[k] == 0 && owned))) return false;
+      }
     }
   }
   const float inv = t ? R.inv[1] : R.inv[0];
@@ -292,7 +310,7 @@ __device__ void overflow_pixel(const Ws& ws, long long pid, unsigned long long* 
 
 // the exact path over the registered pixel list
 template <bool BWD>
-__global__ __launch_bounds__(kOvfThreads) void k_overflow(Ws ws) {
+__global__ __launch_bounds__(kOvfThreads, BWD ? 5 : 7) void k_overflow(Ws ws) {
   pdl_begin();
   __shared__ unsigned long long sbuf[kOvfThreads / 32][kOvfBuf];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
