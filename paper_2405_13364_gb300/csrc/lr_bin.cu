@@ -128,7 +128,7 @@ __device__ __forceinline__ void for_each_ref(const Ws& ws, const ViewDev& V, lon
 
 // count and scatter are latency-bound (gathers, atomics): 5 resident CTAs per SM (48
 // registers, a few spills) measured faster than the 3 that 64-74 registers allow
-__global__ __launch_bounds__(kBinThreads, 5) void k_bin_count(Ws ws) {
+__global__ __launch_bounds__(kBinThreads, kBinMinBlocks) void k_bin_count(Ws ws) {
   pdl_begin();
   __shared__ uint32_t hist[kHistSmemBins];
   const int v = view_of_chunk(ws.views, ws.n_views, blockIdx.x);
@@ -266,7 +266,7 @@ __global__ __launch_bounds__(1024) void k_bin_scan(Ws ws) {
   }
 }
 
-__global__ __launch_bounds__(kBinThreads, 5) void k_bin_scatter(Ws ws) {
+__global__ __launch_bounds__(kBinThreads, kBinMinBlocks) void k_bin_scatter(Ws ws) {
   pdl_begin();
   __shared__ uint32_t hist[kHistSmemBins];
   if (ws.ctrl->error == LR_ERR_OVERFLOW) return;

@@ -47,8 +47,12 @@ constexpr size_t kSortBigSmemBytes =
         ? (size_t)kBucketBigCap * 8 + (2 * (size_t)kBucketsBig + 2) * 4
         : 2 * (size_t)kSortBigCap * 8;
 constexpr int kHistSmemBins = 8192;         // shared-memory bin counters per CTA (Sec. 2 Stage 2)
-constexpr int kChunkQuads = 1024;           // quads per binning CTA
-constexpr int kBinThreads = 256;            // threads per binning CTA
+#ifndef LR_CHUNK_QUADS
+#define LR_CHUNK_QUADS 2048
+#endif
+constexpr int kChunkQuads = LR_CHUNK_QUADS;  // quads per binning CTA
+constexpr int kBinThreads = kChunkQuads / 4 < 1024 ? kChunkQuads / 4 : 1024;   // threads per binning CTA
+constexpr int kBinMinBlocks = kBinThreads >= 1024 ? 1 : (kBinThreads >= 512 ? 2 : 5);
 constexpr int kSmallBins = 4;               // AABB-counted up to kSmallBins x kSmallBins bins
 
 // cull reasons (stats and rec_info bits 8..11)
