@@ -1,7 +1,7 @@
 // lr_bin.cu -- Stage 2 of the pipeline, quad binning (Sec. 2, "Stage 2: quad binning"),
 // plus the per-bin depth sort that feeds Stage 3.
 //
-//   k_bin_count    Phase 1: per-bin reference counts. Each CTA owns a chunk of 1024 quads
+//   k_bin_count    Phase 1: per-bin reference counts. Each CTA owns a chunk of 2048 quads
 //                  of one view and counts into shared-memory bin counters (the paper's
 //                  5120-entry arrays), then adds its non-zero counters to global memory.
 //                  Quads whose bin rectangle is at most 4x4 bins are counted from their
@@ -126,8 +126,8 @@ __device__ __forceinline__ void for_each_ref(const Ws& ws, const ViewDev& V, lon
   }
 }
 
-// count and scatter are latency-bound (gathers, atomics): 5 resident CTAs per SM (48
-// registers, a few spills) measured faster than the 3 that 64-74 registers allow
+// count and scatter are latency-bound (gathers, atomics): chunks of 2048 quads on 512-thread
+// CTAs, two per SM (measured a little faster than 1024 quads on 256 threads or 4096 on 1024)
 __global__ __launch_bounds__(kBinThreads, kBinMinBlocks) void k_bin_count(Ws ws) {
   pdl_begin();
   __shared__ uint32_t hist[kHistSmemBins];
