@@ -385,7 +385,11 @@ typedef struct {
   int32_t poll_interval_us;      /* while batches run, the server thread polls their completion
                                     in a spin for up to this long between looks at the queue
                                     (new requests end the spin early); default 20 */
-  int32_t reserved;
+  int32_t idle_spin_us;          /* with nothing queued or running, the server thread spins this
+                                    long waiting for a request before it sleeps (waking a
+                                    sleeping thread costs tens of microseconds of latency; the
+                                    spin costs one CPU core); 0 = default 5000, -1 = sleep at
+                                    once */
 } lr_server_config;
 
 typedef struct {

@@ -436,13 +436,14 @@ class Server:
 
     def __init__(self, sorter_k: int = 3, num_slots: int = 2, max_batch_views: int = 16,
                  slot_workspace_bytes: int = 512 << 20, poll_interval_us: int = 20,
-                 max_width: int = 2560, max_height: int = 2048, device=None, light=None):
+                 max_width: int = 2560, max_height: int = 2048, device=None, light=None,
+                 idle_spin_us: int = 0):
         self.renderer = Renderer(sorter_k=sorter_k, max_width=max_width, max_height=max_height,
                                  device=device)
         self.ctx = self.renderer.ctx
         if light is not None:      # (x, y, z) toward the light, ambient: for lit requests
             self.renderer.set_lighting(light[:3], light[3])
-        cfg = B.lr_server_config(num_slots, max_batch_views, slot_workspace_bytes, poll_interval_us, 0)
+        cfg = B.lr_server_config(num_slots, max_batch_views, slot_workspace_bytes, poll_interval_us, idle_spin_us)
         B.lr_server_start(self.ctx, cfg)
         self._live = {}
         self.running = True

@@ -94,7 +94,7 @@ class lr_ws_layout(ctypes.Structure):
 class lr_server_config(ctypes.Structure):
     _fields_ = [("num_slots", ctypes.c_int32), ("max_batch_views", ctypes.c_int32),
                 ("slot_workspace_bytes", ctypes.c_int64), ("poll_interval_us", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("idle_spin_us", ctypes.c_int32)]
 
 
 class lr_request_info(ctypes.Structure):

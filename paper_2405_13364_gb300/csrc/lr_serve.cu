@@ -197,7 +197,15 @@ static void serve_loop(lr_server* s) {
       }
       lk.lock();
     } else if (s->queue.empty() && !s->stopping) {
-      s->wake.wait(lk);
+      // idle: spin for a while on the submission flag (a new request is then seen within
+      // microseconds), then sleep until a submission or stop wakes the thread
+      if (s->cfg.idle_spin_us > 0) {
+        lk.unlock();
+        const auto until = std::chrono::steady_clock::now() + std::chrono::microseconds(s->cfg.idle_spin_us);
+        while (!s->submitted.load() && std::chrono::steady_clock::now() < until) std::this_thread::yield();
+        lk.lock();
+      }
+      if (s->queue.empty() && !s->stopping) s->wake.wait(lk);
     }
   }
 }
@@ -226,6 +234,7 @@ extern "C" lr_status lr_server_start(lr_ctx* ctx, const lr_server_config* config
   if (s->cfg.max_batch_views <= 0) s->cfg.max_batch_views = 16;
   if (s->cfg.slot_workspace_bytes <= 0) s->cfg.slot_workspace_bytes = (int64_t)512 << 20;
   if (s->cfg.poll_interval_us <= 0) s->cfg.poll_interval_us = 20;
+  if (s->cfg.idle_spin_us == 0) s->cfg.idle_spin_us = 5000;
   memset(&s->stats, 0, sizeof(s->stats));
   lr_config inner_cfg = *lr_internal_config(ctx);
   inner_cfg.flags &= ~LR_FLAG_TIMING;
