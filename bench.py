@@ -63,12 +63,14 @@ TUNE_KS = (1, 2, 3)
 TUNE_BINS = (16, 32, 64)
 TUNE_CTAS = (0, 2)
 TUNE_BLOCKS = (4, 8)
+TUNE_SHARED = (False, True)
 
 
 def tune_label(t):
     """k<K>[c]_b<bin>[_cta<n>] for one autotuner candidate."""
     return (f"k{t['sorter_k']}{'c' if t['carry_colors'] else ''}_b{t['bin_size']}"
             + (f"_blk8x{t['block_h']}" if t.get("block_h", 4) != 4 else "")
+            + ("_strip" if t.get("shared_setup") else "")
             + (f"_cta{t['raster_ctas_per_sm']}" if t["raster_ctas_per_sm"] else ""))
 
 
@@ -129,12 +131,12 @@ def variant_capture(name: str):
             "source": "ncu capture, K = 1, layers-1080p frame (profiles/)"}
 
 
-def raster_capture(workload: str, k: int, carry: bool, bin_size: int = 32, block_h: int = 4):
+def raster_capture(workload: str, k: int, carry: bool, bin_size: int = 32, block_h: int = 4, shared: bool = False):
     """(traffic bytes, issue-slot utilisation, warp instructions) of the committed ncu
     capture of this rasteriser build (taken with 32-pixel bins), or Nones once the sources
     differ from it or the configuration is another."""
     t = RASTER_TRAFFIC.get((workload, k, carry))
-    if t is None or t[3] != raster_source_hash() or bin_size != 32 or block_h != 4:
+    if t is None or t[3] != raster_source_hash() or bin_size != 32 or block_h != 4 or shared:
         return None, None, None
     return t[0], t[1], t[2]
 
@@ -197,7 +199,7 @@ class ClockSampler:
 
 
 def frame_benchmark(P, torch, scene, k, carry, steps, warmup, flush, dev, dist=None, bin_size=32, ctas=0,
-                    block_h=4):
+                    block_h=4, shared=False):
     """Device-timed frames of one workload: a renderer without per-stage events renders
     `steps` frames (L2 flushed before each, outside the events; CUDA events on the stream
     around each frame), then a second renderer that records an event between stages gives
@@ -205,9 +207,10 @@ def frame_benchmark(P, torch, scene, k, carry, steps, warmup, flush, dev, dist=N
     stage means, the outputs and view of the timed renderer)."""
     W, H = scene.width, scene.height
     ds = P.DeviceScene.from_scene(scene, device=dev)
-    r = P.Renderer(sorter_k=k, carry_colors=carry, bin_size=bin_size, raster_ctas_per_sm=ctas, block_h=block_h)
+    r = P.Renderer(sorter_k=k, carry_colors=carry, bin_size=bin_size, raster_ctas_per_sm=ctas, block_h=block_h,
+                   shared_setup=shared)
     rt = P.Renderer(sorter_k=k, timing=True, carry_colors=carry, bin_size=bin_size, raster_ctas_per_sm=ctas,
-                    block_h=block_h)
+                    block_h=block_h, shared_setup=shared)
     out = r.make_outputs(W, H)
     view = r.view_struct(ds, W, H, out)
     view_t = rt.view_struct(ds, W, H, out)
@@ -245,7 +248,7 @@ def frame_benchmark(P, torch, scene, k, carry, steps, warmup, flush, dev, dist=N
     return sum(ms) / len(ms), st0, stages, sampler, (r, ds, out, view)
 
 
-def raster_roofline(workload, k, carry, frags, raster_ms, sm_count, sm_max_mhz, bin_size=32, block_h=4):
+def raster_roofline(workload, k, carry, frags, raster_ms, sm_count, sm_max_mhz, bin_size=32, block_h=4, shared=False):
     """The rasteriser against the plain-ALU peak: algorithmic lane operations per fragment
     (25 + K) x fragments / its CUDA-event time, against SMs x 128 lanes x the SM clock,
     with the SM count of the device the run is on; plus the instruction-issue ceiling of
@@ -253,7 +256,7 @@ def raster_roofline(workload, k, carry, frags, raster_ms, sm_count, sm_max_mhz, 
     ops = (OPS_PER_FRAG_BASE + k) * frags
     peak = sm_count * LANES_PER_SM_CLK * sm_max_mhz * 1e6 / 1e12   # T lane-ops/s
     achieved = ops / (raster_ms * 1e-3) / 1e12
-    traffic, issue_active, inst = raster_capture(workload, k, carry, bin_size, block_h)
+    traffic, issue_active, inst = raster_capture(workload, k, carry, bin_size, block_h, shared)
     issue_ceiling = None
     if inst:
         ceil_gfrag = sm_count * 4 * sm_max_mhz * 1e6 / (inst / frags) / 1e9
@@ -278,12 +281,13 @@ def particles_benchmark(P, torch, args, flush, dev, sm_count, hbm_gbs):
     scene = scenegen.config_particles_1080p()
     ds = P.DeviceScene.from_scene(scene, device=dev)
     tuned = autotune.tune(ds, scene.width, scene.height, ks=TUNE_KS, ctas_per_sm=TUNE_CTAS, reps=3, device=dev,
-                          bin_sizes=TUNE_BINS, block_hs=TUNE_BLOCKS, use_cache=False)
+                          bin_sizes=TUNE_BINS, block_hs=TUNE_BLOCKS, shared=TUNE_SHARED, use_cache=False)
     del ds
     k, carry = tuned["sorter_k"], bool(tuned.get("carry_colors"))
     ms, st0, stages, sampler, (r, _, _, _) = frame_benchmark(P, torch, scene, k, carry, min(args.steps, 20),
                                                              args.warmup, flush, dev, None, tuned["bin_size"],
-                                                             tuned["raster_ctas_per_sm"], tuned["block_h"])
+                                                             tuned["raster_ctas_per_sm"], tuned["block_h"],
+                                                             bool(tuned["shared_setup"]))
     r.close()
     frags = st0["fragments"]
     clocks = sampler.summary()
@@ -291,12 +295,13 @@ def particles_benchmark(P, torch, args, flush, dev, sm_count, hbm_gbs):
             "quads": scene.num_quads, "fragments_per_frame": frags, "ms_per_frame": round(ms, 4),
             "gfrag_s": round(frags / (ms * 1e-3) / 1e9, 3), "sorter_k": k, "carry_colors": carry,
             "bin_size": tuned["bin_size"], "raster_ctas_per_sm": tuned["raster_ctas_per_sm"],
-            "block": f"8x{tuned['block_h']}",
+            "block": f"8x{tuned['block_h']}", "shared_setup": bool(tuned["shared_setup"]),
             "autotune_ms": {tune_label(t): round(t["ms"], 4) for t in tuned["table"]},
             "stage_ms": stages, "overflow_pixels": st0["overflow_pixels"], "bins_high": st0["bins_high"],
             "sort_bins": st0["sort_bins"],
             "roofline": raster_roofline("particles", k, carry, frags, stages["raster"], sm_count,
-                                        clocks.get("sm_max_mhz") or 2070.0, tuned["bin_size"], tuned["block_h"]),
+                                        clocks.get("sm_max_mhz") or 2070.0, tuned["bin_size"], tuned["block_h"],
+                                        bool(tuned["shared_setup"])),
             **stage_rooflines(scene, st0, stages, hbm_gbs), "clocks": clocks}
 
 
@@ -560,16 +565,17 @@ def run_gpu(args):
         # same exact result; it only moves pixels between the sorter and the exact path)
         from paper_2405_13364_gb300 import autotune
         tuned = autotune.tune(ds, W, H, ks=TUNE_KS, ctas_per_sm=TUNE_CTAS, reps=3, device=dev,
-                              bin_sizes=TUNE_BINS, block_hs=TUNE_BLOCKS, use_cache=False)
+                              bin_sizes=TUNE_BINS, block_hs=TUNE_BLOCKS, shared=TUNE_SHARED, use_cache=False)
         args.k = tuned["sorter_k"]
     carry = bool(tuned and tuned.get("carry_colors"))
     bin_size = tuned["bin_size"] if tuned else 32
     ctas = tuned["raster_ctas_per_sm"] if tuned else 0
     block_h = tuned["block_h"] if tuned else 4
+    shared = bool(tuned["shared_setup"]) if tuned else False
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     ms_frame, st0, stages, sampler, (r, ds, out, view) = frame_benchmark(
-        P, torch, scene, args.k, carry, args.steps, args.warmup, flush, dev, dist, bin_size, ctas, block_h)
+        P, torch, scene, args.k, carry, args.steps, args.warmup, flush, dev, dist, bin_size, ctas, block_h, shared)
     frags = st0["fragments"]
     from paper_2405_13364_gb300 import replicas
     ms_step = replicas.max_over_ranks(ms_frame, dist, dev)
@@ -650,7 +656,7 @@ def run_gpu(args):
     clocks = sampler.summary()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     roofline = raster_roofline(args.workload, args.k, carry, frags, stages["raster"], sm_count,
-                               clocks.get("sm_max_mhz") or 2070.0, bin_size, block_h)
+                               clocks.get("sm_max_mhz") or 2070.0, bin_size, block_h, shared)
     peaks = _measured_peaks()
     hbm = peaks.get("hbm_gbs") if peaks else None
     particles = None
@@ -782,7 +788,7 @@ def run_gpu(args):
         "config": {"workload": WORKLOADS[args.workload][0], "frame": f"{W}x{H}", "quads": scene.num_quads,
                    "fragments_per_frame": frags, "sorter_k": args.k,
                    "carry_colors": carry,
-                   "bin_size": bin_size, "raster_ctas_per_sm": ctas, "block": f"8x{block_h}",
+                   "bin_size": bin_size, "raster_ctas_per_sm": ctas, "block": f"8x{block_h}", "shared_setup": shared,
                    "autotune_ms": None if tuned is None else {tune_label(t): round(t["ms"], 4) for t in tuned["table"]},
                    "l2": "flushed before every step (512 MiB write, outside the timed events)",
                    "parallelism": f"replicas x{world} (one frame per GPU per step)"},

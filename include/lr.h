@@ -102,6 +102,13 @@ typedef struct {
                                 exact renders with flat or per-vertex colours and sorter_k
                                 1, 2 or 3; other renders of the context use 8x4. The image
                                 is the same either way. */
+  int32_t shared_setup;      /* 1: a CTA of 8 warps rasterises a 32x8 strip of a bin (one 8x4
+                                half-block per warp) and sets each candidate triangle up once
+                                for the strip in shared memory (Sec. 2, Stage 3: a bin's
+                                workgroup sets up its triangles together); forward exact
+                                renders with flat or per-vertex colours, sorter_k 1-3 and
+                                32-pixel bins, the others as without it. 0 (default): every
+                                warp sets up its half-block's candidates itself. */
 } lr_config;
 
 /* A quad scene (Sec. 2: quads, not triangles, are the input primitive). Device memory. */

@@ -102,7 +102,7 @@ class Renderer:
     def __init__(self, sorter_k: int = 3, max_width: int = 2560, max_height: int = 2048,
                  timing: bool = False, ref_factor: int = 4, raster_ctas_per_sm: int = 0,
                  device=None, carry_colors: bool = False, alpha_threshold: bool = False,
-                 bin_size: int = 32, block_h: int = 4):
+                 bin_size: int = 32, block_h: int = 4, shared_setup: bool = False):
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
         B.load()
@@ -110,11 +110,12 @@ class Renderer:
             flags = ((LR_FLAG_TIMING if timing else 0) | (B.LR_FLAG_CARRY_COLORS if carry_colors else 0)
                      | (B.LR_FLAG_ALPHA_THRESHOLD if alpha_threshold else 0))
             cfg = lr_config(max_width, max_height, sorter_k, raster_ctas_per_sm, ref_factor,
-                            flags, self.device.index, bin_size, block_h)
+                            flags, self.device.index, bin_size, block_h, int(shared_setup))
             self.ctx = B.lr_create(cfg)
         self.sorter_k = sorter_k
         self.bin_size = bin_size
         self.block_h = block_h
+        self.shared_setup = shared_setup
         self._ws = None
         self._ws_bytes = 0
 

@@ -46,7 +46,7 @@ class lr_config(ctypes.Structure):
     _fields_ = [("max_width", ctypes.c_int32), ("max_height", ctypes.c_int32),
                 ("sorter_k", ctypes.c_int32), ("raster_ctas_per_sm", ctypes.c_int32),
                 ("ref_factor", ctypes.c_int32), ("flags", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("bin_size", ctypes.c_int32), ("block_h", ctypes.c_int32)]
+                ("bin_size", ctypes.c_int32), ("block_h", ctypes.c_int32), ("shared_setup", ctypes.c_int32)]
 
 
 class lr_quads(ctypes.Structure):

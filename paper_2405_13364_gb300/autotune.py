@@ -8,7 +8,8 @@ persistent rasteriser CTAs per SM, and for flat-colour scenes whether the sorter
 colours. Every candidate gives the same coverage and the same exact fragment order; K only
 moves pixels between the sorter and the exact overflow path, whose composite sums in a
 different order, so colours agree to fp32 rounding (the tuner checks 1e-5, the accuracy
-bar) rather than bit for bit. The work item is an 8x4 half-block or an 8x8 block.
+bar) rather than bit for bit. The work item is an 8x4 half-block per warp, an 8x8 block per
+warp, or (shared set-up) a 32x8 strip per CTA whose candidates the CTA sets up together.
 
 The tuner renders the workload with every candidate, checks that all candidates produce
 the same image within 1e-5, times each with CUDA events (median of `reps`), and caches the
@@ -62,12 +63,13 @@ def lookup(width, height, num_quads, color_mode, device=None):
 
 
 def tune(scene, width: int, height: int, ks=DEFAULT_KS, ctas_per_sm=(0,), reps: int = 5,
-         use_cache: bool = True, device=None, carry=None, bin_sizes=(32,), block_hs=(4,)):
+         use_cache: bool = True, device=None, carry=None, bin_sizes=(32,), block_hs=(4,), shared=(False,)):
     """scene: a DeviceScene. Returns {'sorter_k', 'raster_ctas_per_sm', 'carry_colors',
     'bin_size', 'block_h', 'ms', 'table'}. carry: candidates for carrying flat colours in the
     sorter (default: both for flat-colour scenes). bin_sizes: candidate bin sizes (16, 32,
     64). block_hs: candidate work-item heights (4: 8x4 half-blocks, 8: 8x8 blocks, built
-    for sorter capacities up to 3)."""
+    for sorter capacities up to 3). shared: whether a CTA sets candidates up once per 32x8
+    strip (lr_config.shared_setup; 32-pixel bins, 8x4 half-blocks, capacities up to 3)."""
     from . import Renderer
     key = workload_key(width, height, scene.num_quads, scene.color_mode, device)
     cache = _load_cache() if use_cache else {}
@@ -77,12 +79,13 @@ def tune(scene, width: int, height: int, ks=DEFAULT_KS, ctas_per_sm=(0,), reps: 
     ref_img = None
     if carry is None:
         carry = (False, True) if scene.color_mode == 0 else (False,)
-    cands = [(k, c, cc, bs, bh) for bh in block_hs for bs in bin_sizes for k in ks for c in ctas_per_sm
-             for cc in carry if bh == 4 or k <= 3]
-    for k, c, cc, bs, bh in cands:
+    cands = [(k, c, cc, bs, bh, sh) for sh in shared for bh in block_hs for bs in bin_sizes for k in ks
+             for c in ctas_per_sm for cc in carry
+             if (bh == 4 or k <= 3) and (not sh or (bs == 32 and bh == 4 and k <= 3))]
+    for k, c, cc, bs, bh, sh in cands:
         if True:
             r = Renderer(sorter_k=k, raster_ctas_per_sm=c, device=device, carry_colors=cc, bin_size=bs,
-                         block_h=bh)
+                         block_h=bh, shared_setup=sh)
             out = r.make_outputs(width, height)
             view = r.view_struct(scene, width, height, out)
             st = r.render_views([view])                    # sizes the workspace, checked
@@ -101,11 +104,13 @@ def tune(scene, width: int, height: int, ks=DEFAULT_KS, ctas_per_sm=(0,), reps: 
                 times.append(a.elapsed_time(b))
             ovf = B_overflow(r)
             table.append(dict(sorter_k=k, raster_ctas_per_sm=c, carry_colors=cc, bin_size=bs, block_h=bh,
+                              shared_setup=sh,
                               ms=statistics.median(times), overflow_pixels=ovf, fragments=int(st.fragments)))
             r.close()
     best = min(table, key=lambda t: t["ms"])
     result = dict(sorter_k=best["sorter_k"], raster_ctas_per_sm=best["raster_ctas_per_sm"],
                   carry_colors=best["carry_colors"], bin_size=best["bin_size"], block_h=best["block_h"],
+                  shared_setup=best["shared_setup"],
                   ms=best["ms"], table=table)
     if use_cache:
         cache[key] = result

@@ -52,6 +52,12 @@ LR_DECLARE_RASTER(12)
 LR_DECLARE_RASTER8(1)
 LR_DECLARE_RASTER8(2)
 LR_DECLARE_RASTER8(3)
+#define LR_DECLARE_RASTER_STRIP(KK)                                                               \
+  cudaError_t prepare_raster_strip_##KK(int* blocks_flat, int* blocks_vtx);                       \
+  cudaError_t launch_raster_strip_##KK(int mode, const Ws& ws, int grid, cudaStream_t st);
+LR_DECLARE_RASTER_STRIP(1)
+LR_DECLARE_RASTER_STRIP(2)
+LR_DECLARE_RASTER_STRIP(3)
 
 __global__ void k_write_views(ViewChunk chunk, ViewDev* dst) {
   pdl_begin();
@@ -71,16 +77,18 @@ struct RasterVariant {
   LaunchFn launch;
   Prepare8Fn prepare8;
   LaunchFn launch8;
+  Prepare8Fn prepare_strip;   // the per-strip shared set-up (lr_raster_strip.cuh)
+  LaunchFn launch_strip;
 };
 
 static const RasterVariant kVariants[] = {
-    {1, prepare_raster_1, launch_raster_1, prepare_raster8_1, launch_raster8_1},
-    {2, prepare_raster_2, launch_raster_2, prepare_raster8_2, launch_raster8_2},
-    {3, prepare_raster_3, launch_raster_3, prepare_raster8_3, launch_raster8_3},
-    {4, prepare_raster_4, launch_raster_4, nullptr, nullptr},
-    {6, prepare_raster_6, launch_raster_6, nullptr, nullptr},
-    {8, prepare_raster_8, launch_raster_8, nullptr, nullptr},
-    {12, prepare_raster_12, launch_raster_12, nullptr, nullptr},
+    {1, prepare_raster_1, launch_raster_1, prepare_raster8_1, launch_raster8_1, prepare_raster_strip_1, launch_raster_strip_1},
+    {2, prepare_raster_2, launch_raster_2, prepare_raster8_2, launch_raster8_2, prepare_raster_strip_2, launch_raster_strip_2},
+    {3, prepare_raster_3, launch_raster_3, prepare_raster8_3, launch_raster8_3, prepare_raster_strip_3, launch_raster_strip_3},
+    {4, prepare_raster_4, launch_raster_4, nullptr, nullptr, nullptr, nullptr},
+    {6, prepare_raster_6, launch_raster_6, nullptr, nullptr, nullptr, nullptr},
+    {8, prepare_raster_8, launch_raster_8, nullptr, nullptr, nullptr, nullptr},
+    {12, prepare_raster_12, launch_raster_12, nullptr, nullptr, nullptr, nullptr},
 };
 
 struct Layout {
@@ -193,6 +201,7 @@ struct VariantState {
   const RasterVariant* v = nullptr;
   int flat = 1, vtx = 1, bwd = 1, lit = 1;
   int flat8 = 1, vtx8 = 1;     // the 8x8-block kernels (when the capacity has them)
+  int flat_s = 1, vtx_s = 1;   // the strip kernels
 };
 
 struct lr_ctx {
@@ -249,7 +258,7 @@ extern "C" lr_status lr_create(const lr_config* config, lr_ctx** out_ctx) {
   if (g.block_h <= 0) g.block_h = kHbH;
   c->bin_log2 = g.bin_size == 16 ? 4 : (g.bin_size == 32 ? 5 : (g.bin_size == 64 ? 6 : -1));
   if (g.max_width > 65535 || g.max_height > 65535 || g.raster_ctas_per_sm < 0 || c->bin_log2 < 0 ||
-      (g.block_h != 4 && g.block_h != 8)) {
+      (g.block_h != 4 && g.block_h != 8) || g.shared_setup < 0 || g.shared_setup > 1) {
     delete c;
     return LR_ERR_INVALID_ARG;
   }
@@ -273,7 +282,8 @@ extern "C" lr_status lr_create(const lr_config* config, lr_ctx** out_ctx) {
     V.v = &kVariants[i];
     e = V.v->prepare(&V.flat, &V.vtx, &V.bwd, &V.lit);
     if (e == cudaSuccess && V.v->prepare8 && g.block_h == 8) e = V.v->prepare8(&V.flat8, &V.vtx8);
-    int* all[] = {&V.flat, &V.vtx, &V.bwd, &V.lit, &V.flat8, &V.vtx8};
+    if (e == cudaSuccess && V.v->prepare_strip && g.shared_setup) e = V.v->prepare_strip(&V.flat_s, &V.vtx_s);
+    int* all[] = {&V.flat, &V.vtx, &V.bwd, &V.lit, &V.flat8, &V.vtx8, &V.flat_s, &V.vtx_s};
     for (int* x : all) {
       if (g.raster_ctas_per_sm > 0) *x = std::min(*x, g.raster_ctas_per_sm);
       *x = std::max(*x, 1);
@@ -579,10 +589,15 @@ static lr_status launch_sequence(lr_ctx* ctx, const Prepared& P, cudaStream_t st
   const int mode = bwd ? 2 : (P.any_lit ? 17 : ((carry ? 1 : 0) | (P.any_hash ? 4 : 0) | (ath ? 8 : 0)));
   ws.t_min = ath ? kAlphaTMin : 0.0f;
   const VariantState& VS = ctx->vs[P.variant];
-  // 8x8 blocks for forward exact renders of flat or carried colours, when asked for and built
-  const bool blk8 = ctx->cfg.block_h == 8 && VS.v->launch8 && !bwd && !ath && !P.any_lit;
+  // the strip kernel (32-pixel bins) or 8x8 blocks for forward exact renders of flat or
+  // carried colours, when asked for and built
+  const bool strip = ctx->cfg.shared_setup && VS.v->launch_strip && !bwd && !ath && !P.any_lit &&
+                     ctx->bin_log2 == kBinLog2Default;
+  const bool blk8 = !strip && ctx->cfg.block_h == 8 && VS.v->launch8 && !bwd && !ath && !P.any_lit;
   cudaError_t e;
-  if (blk8) {
+  if (strip) {
+    e = VS.v->launch_strip(mode, ws, ctx->sms * (carry ? VS.vtx_s : VS.flat_s), st);
+  } else if (blk8) {
     e = VS.v->launch8(mode, ws, ctx->sms * (carry ? VS.vtx8 : VS.flat8), st);
   } else {
     const int rblocks = bwd ? VS.bwd : (P.any_lit ? VS.lit : (carry ? VS.vtx : VS.flat));

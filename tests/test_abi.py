@@ -48,7 +48,7 @@ def test_binding_covers_every_symbol():
 def test_struct_sizes_match_header_layout(lib):
     from paper_2405_13364_gb300 import _binding as B
     # plain C layout expectations (x86-64 and aarch64 LP64 agree)
-    assert ctypes.sizeof(B.lr_config) == 9 * 4
+    assert ctypes.sizeof(B.lr_config) == 10 * 4
     assert ctypes.sizeof(B.lr_quads) == 6 * 8
     assert ctypes.sizeof(B.lr_camera) == 18 * 4
     assert ctypes.sizeof(B.lr_target) == 5 * 8
