@@ -10,11 +10,19 @@
 
 namespace lr {
 
+#ifndef LR_OVF_BUF
+#define LR_OVF_BUF 512
+#endif
+// per-warp buffer of the exact path (a power of two; a pass composites 15/32 of it): 512
+// entries (4 KB) let seven CTAs of four warps share an SM (registers and shared memory), so
+// up to 4,256 registered pixels of a frame run in one wave, one warp each
+constexpr int kExactBuf = LR_OVF_BUF;
+
 // the exact path over the registered pixel list
 template <bool BWD>
 __global__ __launch_bounds__(kOvfThreads, BWD ? 5 : 7) void k_overflow(Ws ws) {
   pdl_begin();
-  __shared__ unsigned long long sbuf[kOvfThreads / 32][kOvfBuf];
+  __shared__ unsigned long long sbuf[kOvfThreads / 32][kExactBuf];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
   const unsigned long long total = ws.ctrl->ovf_count;
@@ -23,7 +31,7 @@ __global__ __launch_bounds__(kOvfThreads, BWD ? 5 : 7) void k_overflow(Ws ws) {
     if (lane == 0) item = atomicAdd(&ws.ctrl->ovf_head, 1ull);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= total) break;
-    overflow_pixel<BWD, kOvfBuf>(ws, (long long)ws.ovf_list[item], sbuf[warp]);
+    overflow_pixel<BWD, kExactBuf>(ws, (long long)ws.ovf_list[item], sbuf[warp]);
   }
 }
 
