@@ -19,8 +19,8 @@
 //   k_bin_sort     Stage-1 depth sort: sorts each bin's references ascending, i.e. front
 //                  to back by a representative depth, ties with the higher quad index
 //                  first. Bins with fewer than 2048 references: one 256-thread CTA per
-//                  bin, a merge sort in shared memory (warp-sorted 32-key runs, then
-//                  merge-path levels).
+//                  bin, a merge sort in shared memory (256-key runs sorted in registers
+//                  by one warp each, then merge-path levels).
 //   k_bin_sort_big The high-density bins (2048 references or more; the paper's "high"
 //                  category): persistent 1024-thread CTAs take them from the front of the
 //                  size-ordered bin list. Up to 20480 references are bucket-sorted in
@@ -493,35 +493,68 @@ __device__ bool cta_bucket_sort(unsigned long long* r, int n, unsigned long long
   return true;
 }
 
-// Ascending merge sort of g[0, n) (n <= kSortBigCap) in shared memory by the whole CTA:
-// 32-key runs sorted by warp shuffles, then merge levels between two shared buffers, each
-// thread producing an equal slice of every level's output (merge path search + a
-// sequential merge of its slice). The keys are padded to a power of two N with the
-// largest key, so every output position from n on holds padding at every level: both
-// buffers are padded once, and the runs and output slices starting at n or later are
-// skipped.
+// Ascending sort of the 256 keys v (eight per lane, lane l holding elements 8 l .. 8 l + 7)
+// by one warp: a bitonic network, its compare-exchanges between a lane's own keys (element
+// distance below 8) in registers and the others by shuffles with the partner lane.
+__device__ __forceinline__ void warp_bitonic256(unsigned long long v[8], int lane) {
+#pragma unroll
+  for (int k = 2; k <= 256; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j < 8) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          if (r & j) continue;   // r is the lower element of the pair (r, r + j)
+          // ascending where element 8 lane + r has bit k clear
+          const bool asc = k < 8 ? (r & k) == 0 : (lane & (k >> 3)) == 0;
+          const unsigned long long a = v[r], b = v[r | j];
+          const bool sw = asc ? (a > b) : (a < b);
+          v[r] = sw ? b : a;
+          v[r | j] = sw ? a : b;
+        }
+      } else {
+        const int lj = j >> 3;
+        const bool asc = (lane & (k >> 3)) == 0;
+        const bool lower = (lane & lj) == 0;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[r], lj);
+          // the lower element of an ascending pair (or the upper of a descending one) keeps
+          // the smaller key
+          v[r] = (asc == lower) ? (v[r] < o ? v[r] : o) : (v[r] > o ? v[r] : o);
+        }
+      }
+    }
+  }
+}
+
+// Ascending merge sort of g[0, n) (n <= 256 * warps of the CTA) in shared memory by the whole
+// CTA: 256-key runs sorted in registers, one per warp (warp_bitonic256), then merge levels
+// between two shared buffers, each thread producing an equal slice of every level's output
+// (merge path search + a sequential merge of its slice). The keys are padded to a power of
+// two N >= 256 with the largest key, so every output position from n on holds padding at
+// every level: both buffers are padded once, and the runs and output slices starting at n
+// or later are skipped.
 __device__ __forceinline__ void cta_merge_sort_smem(unsigned long long* g, int n, unsigned long long* A,
                                     unsigned long long* Bf) {
-  int N = 32;
+  int N = 256;
   while (N < n) N <<= 1;
   const int T = (int)blockDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = T >> 5;
-  for (int i = t; i < N; i += T) A[i] = i < n ? g[i] : ~0ull;
-  for (int i = n + t; i < N; i += T) Bf[i] = ~0ull;
-  __syncthreads();
-  for (int r = warp; 32 * r < n; r += nw) {
-    unsigned long long v = A[32 * r + lane];
-    for (int k = 2; k <= 32; k <<= 1)
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, j);
-        const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
-        v = keep_min ? (v < w ? v : w) : (v > w ? v : w);
-      }
-    A[32 * r + lane] = v;
+  for (int r = warp; 256 * r < n; r += nw) {
+    unsigned long long v[8];
+    const int base = 256 * r + 8 * lane;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = base + k < n ? g[base + k] : ~0ull;
+    warp_bitonic256(v, lane);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) A[base + k] = v[k];
   }
+  for (int i = ((n + 255) & ~255) + t; i < N; i += T) A[i] = ~0ull;
+  for (int i = n + t; i < N; i += T) Bf[i] = ~0ull;
   __syncthreads();
   unsigned long long* src = A;
   unsigned long long* dst = Bf;
-  for (int w = 32; w < N; w <<= 1) {
+  for (int w = 256; w < N; w <<= 1) {
     const int P = N / T > 0 ? N / T : 1;      // outputs per thread; divides 2w
     for (int d0 = t * P; d0 < n; d0 += T * P) {
       const int base = (d0 / (2 * w)) * (2 * w), loc = d0 - base;
@@ -562,7 +595,10 @@ __device__ __forceinline__ bool bin_owned(const Ws& ws, int bin) {
   return false;
 }
 
-__global__ __launch_bounds__(256) void k_bin_sort(Ws ws) {
+#ifndef LR_SORT_MIN_BLOCKS
+#define LR_SORT_MIN_BLOCKS 5   // resident CTAs per SM (48 registers, no spills)
+#endif
+__global__ __launch_bounds__(256, LR_SORT_MIN_BLOCKS) void k_bin_sort(Ws ws) {
   pdl_begin();
   extern __shared__ unsigned long long sbuf[];
   if (ws.ctrl->error == LR_ERR_OVERFLOW) return;
