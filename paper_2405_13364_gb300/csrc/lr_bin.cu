@@ -19,8 +19,8 @@
 //   k_bin_sort     Stage-1 depth sort: sorts each bin's references ascending, i.e. front
 //                  to back by a representative depth, ties with the higher quad index
 //                  first. Bins with fewer than 2048 references: one 256-thread CTA per
-//                  bin, a merge sort in shared memory (256-key runs sorted in registers
-//                  by one warp each, then merge-path levels).
+//                  bin, a merge sort in shared memory (runs of 64 to 256 keys sorted in
+//                  registers by one warp each, then merge-path levels).
 //   k_bin_sort_big The high-density bins (2048 references or more; the paper's "high"
 //                  category): persistent 1024-thread CTAs take them from the front of the
 //                  size-ordered bin list. Up to 20480 references are bucket-sorted in
@@ -493,31 +493,33 @@ __device__ bool cta_bucket_sort(unsigned long long* r, int n, unsigned long long
   return true;
 }
 
-// Ascending sort of the 256 keys v (eight per lane, lane l holding elements 8 l .. 8 l + 7)
-// by one warp: a bitonic network, its compare-exchanges between a lane's own keys (element
-// distance below 8) in registers and the others by shuffles with the partner lane.
-__device__ __forceinline__ void warp_bitonic256(unsigned long long v[8], int lane) {
+// Ascending sort of the 32 KPL keys v (KPL per lane, lane l holding elements KPL l ..
+// KPL l + KPL - 1) by one warp: a bitonic network, its compare-exchanges between a lane's own
+// keys (element distance below KPL) in registers and the others by shuffles with the
+// partner lane.
+template <int KPL>
+__device__ __forceinline__ void warp_bitonic(unsigned long long v[KPL], int lane) {
 #pragma unroll
-  for (int k = 2; k <= 256; k <<= 1) {
+  for (int k = 2; k <= 32 * KPL; k <<= 1) {
 #pragma unroll
     for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j < 8) {
+      if (j < KPL) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
+        for (int r = 0; r < KPL; ++r) {
           if (r & j) continue;   // r is the lower element of the pair (r, r + j)
-          // ascending where element 8 lane + r has bit k clear
-          const bool asc = k < 8 ? (r & k) == 0 : (lane & (k >> 3)) == 0;
+          // ascending where element KPL lane + r has bit k clear
+          const bool asc = k < KPL ? (r & k) == 0 : (lane & (k / KPL)) == 0;
           const unsigned long long a = v[r], b = v[r | j];
           const bool sw = asc ? (a > b) : (a < b);
           v[r] = sw ? b : a;
           v[r | j] = sw ? a : b;
         }
       } else {
-        const int lj = j >> 3;
-        const bool asc = (lane & (k >> 3)) == 0;
+        const int lj = j / KPL;
+        const bool asc = (lane & (k / KPL)) == 0;
         const bool lower = (lane & lj) == 0;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
+        for (int r = 0; r < KPL; ++r) {
           const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[r], lj);
           // the lower element of an ascending pair (or the upper of a descending one) keeps
           // the smaller key
@@ -528,33 +530,46 @@ __device__ __forceinline__ void warp_bitonic256(unsigned long long v[8], int lan
   }
 }
 
+// Runs of 32 KPL keys of g[0, n), one warp each, sorted into A (padded with the largest key
+// up to the end of the last run).
+template <int KPL>
+__device__ __forceinline__ void sort_runs(const unsigned long long* g, int n, unsigned long long* A) {
+  constexpr int L = 32 * KPL;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = warp; L * r < n; r += nw) {
+    unsigned long long v[KPL];
+    const int base = L * r + KPL * lane;
+#pragma unroll
+    for (int k = 0; k < KPL; ++k) v[k] = base + k < n ? g[base + k] : ~0ull;
+    warp_bitonic<KPL>(v, lane);
+#pragma unroll
+    for (int k = 0; k < KPL; ++k) A[base + k] = v[k];
+  }
+}
+
 // Ascending merge sort of g[0, n) (n <= 256 * warps of the CTA) in shared memory by the whole
-// CTA: 256-key runs sorted in registers, one per warp (warp_bitonic256), then merge levels
-// between two shared buffers, each thread producing an equal slice of every level's output
-// (merge path search + a sequential merge of its slice). The keys are padded to a power of
-// two N >= 256 with the largest key, so every output position from n on holds padding at
-// every level: both buffers are padded once, and the runs and output slices starting at n
-// or later are skipped.
+// CTA: runs sorted in registers, one per warp (sort_runs), then merge levels between two
+// shared buffers, each thread producing an equal slice of every level's output (merge path
+// search + a sequential merge of its slice). Runs are 256 keys long when nearly every warp
+// gets one, else 128 or 64 (a warp without a run would wait at the barrier). The keys are
+// padded to a power of two N with the largest key, so every output position from n on
+// holds padding at every level: both buffers are padded once, and the runs and output
+// slices starting at n or later are skipped.
 __device__ __forceinline__ void cta_merge_sort_smem(unsigned long long* g, int n, unsigned long long* A,
                                     unsigned long long* Bf) {
-  int N = 256;
+  const int T = (int)blockDim.x, t = threadIdx.x, nw = T >> 5;
+  const int run = n > (nw - 1) * 256 ? 256 : (n > (nw - 1) * 128 ? 128 : 64);
+  int N = run;
   while (N < n) N <<= 1;
-  const int T = (int)blockDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = T >> 5;
-  for (int r = warp; 256 * r < n; r += nw) {
-    unsigned long long v[8];
-    const int base = 256 * r + 8 * lane;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = base + k < n ? g[base + k] : ~0ull;
-    warp_bitonic256(v, lane);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) A[base + k] = v[k];
-  }
-  for (int i = ((n + 255) & ~255) + t; i < N; i += T) A[i] = ~0ull;
+  if (run == 256) sort_runs<8>(g, n, A);
+  else if (run == 128) sort_runs<4>(g, n, A);
+  else sort_runs<2>(g, n, A);
+  for (int i = ((n + run - 1) / run) * run + t; i < N; i += T) A[i] = ~0ull;
   for (int i = n + t; i < N; i += T) Bf[i] = ~0ull;
   __syncthreads();
   unsigned long long* src = A;
   unsigned long long* dst = Bf;
-  for (int w = 256; w < N; w <<= 1) {
+  for (int w = run; w < N; w <<= 1) {
     const int P = N / T > 0 ? N / T : 1;      // outputs per thread; divides 2w
     for (int d0 = t * P; d0 < n; d0 += T * P) {
       const int base = (d0 / (2 * w)) * (2 * w), loc = d0 - base;

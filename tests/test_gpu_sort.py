@@ -4,8 +4,9 @@ ascending (the keys are distinct: representative depth, then quad index), hold e
 (quad, bin) pair at most once, and only name visible quads whose pixel box meets the bin.
 The image does not show a wrong order (the exact path repairs every misordered pixel), so
 these lists are checked directly, on scenes that take every branch of the sort: a few
-references, one to eight warps' runs of 256, the dense-bin bucket sort, the merge in shared
-memory alone (equal depths) and the merge through global memory.
+references, register-sorted runs of 64, 128 and 256 keys with zero to five merge levels, the
+dense-bin bucket sort, the merge in shared memory alone (equal depths) and the merge through
+global memory.
 """
 import numpy as np
 import pytest
@@ -80,7 +81,7 @@ def _particles_in_one_bin(n, seed):
     return scenegen.gaussian_particles(n, 32, 32, seed=seed, sigma=1.5, size_px=(2.0, 4.0))
 
 
-@pytest.mark.parametrize("n,branch", [(40, None), (200, None), (700, None), (1900, None),
+@pytest.mark.parametrize("n,branch", [(40, None), (200, None), (700, None), (1300, None), (1900, None),
                                       (6000, 0), (30000, 2)])
 def test_one_bin_sorted(lr, n, branch):
     s = _particles_in_one_bin(n, seed=40 + n % 17)
