@@ -91,17 +91,31 @@ __device__ __forceinline__ unsigned long long ref_key(float rep, long long q) {
 // Shared by count and scatter: for each (visible quad, touched bin) of the CTA's chunk
 // call f(q, local_bin, bx, by). Small quads enumerate their AABB bins in their own
 // thread; large quads are processed by the whole warp, one bin per lane.
-template <typename F>
+// PF: the next iteration's rectangle and info are loaded while this one's bins are handled
+// (the count's loop is latency-bound, a dependent load per iteration otherwise: 18.4 -> 17.0
+// µs on the layer frame; the scatter, with more live registers, measured no faster with it).
+template <bool PF, typename F>
 __device__ __forceinline__ void for_each_ref(const Ws& ws, const ViewDev& V, long long q0, long long q1,
                                              F&& f) {
   const int lane = threadIdx.x & 31;
   const int lg = ws.bin_log2;
-  for (long long base = q0 + (threadIdx.x & ~31); base < q1; base += blockDim.x) {
+  long long base = q0 + (threadIdx.x & ~31);
+  uint2 rect_n = make_uint2(kRectInvisible, kRectInvisible);
+  uint32_t info_n = 0;
+  if (PF && base + lane < q1) { rect_n = ws.rec_rect[base + lane]; info_n = ws.rec_info[base + lane]; }
+  for (; base < q1; base += blockDim.x) {
     const long long q = base + lane;
     const bool in = q < q1;
-    uint2 rect = make_uint2(kRectInvisible, kRectInvisible);
-    uint32_t info = 0;
-    if (in) { rect = ws.rec_rect[q]; info = ws.rec_info[q]; }
+    uint2 rect = rect_n;
+    uint32_t info = info_n;
+    if (PF) {
+      rect_n = make_uint2(kRectInvisible, kRectInvisible);
+      info_n = 0;
+      if (q + blockDim.x < q1) { rect_n = ws.rec_rect[q + blockDim.x]; info_n = ws.rec_info[q + blockDim.x]; }
+    } else if (in) {
+      rect = ws.rec_rect[q];
+      info = ws.rec_info[q];
+    }
     const bool vis = in && rect.x != kRectInvisible;
     const int px0 = rect.x & 0xffff, px1 = rect.x >> 16, py0 = rect.y & 0xffff, py1 = rect.y >> 16;
     if (vis && !(info & kInfoLarge)) {
@@ -140,7 +154,7 @@ __global__ __launch_bounds__(kBinThreads, kBinMinBlocks) void k_bin_count(Ws ws)
   if (smem)
     for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0u;
   __syncthreads();
-  for_each_ref(ws, V, q0, q1, [&](long long, int b, int, int, uint2, uint32_t) {
+  for_each_ref<true>(ws, V, q0, q1, [&](long long, int b, int, int, uint2, uint32_t) {
     if (smem) atomicAdd(&hist[b], 1u);
     else atomicAdd(&ws.bin_count[V.bin_base + b], 1u);
   });
@@ -286,7 +300,7 @@ __global__ __launch_bounds__(kBinThreads, kBinMinBlocks) void k_bin_scatter(Ws w
     }
     __syncthreads();
   }
-  for_each_ref(ws, V, q0, q1, [&](long long q, int b, int bx, int by, uint2 rect, uint32_t info) {
+  for_each_ref<false>(ws, V, q0, q1, [&](long long q, int b, int bx, int by, uint2 rect, uint32_t info) {
     const uint32_t slot = smem ? atomicAdd(&hist[b], 1u) : atomicAdd(&ws.bin_cursor[V.bin_base + b], 1u);
     const int lg = ws.bin_log2;
     const int x0 = max((int)(rect.x & 0xffff), bx << lg);
