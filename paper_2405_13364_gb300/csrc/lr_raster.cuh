@@ -311,9 +311,16 @@ struct PixelState {
   bool flagged;
   GradPixel gp;
 
+  // K = 1, forward, colours carried: the empty slot holds a fully transparent colour, so
+  // blending it changes nothing (T and the colour stay, last is still kSent) and the in-order
+  // insert needs no test for it (layer frame rasteriser 0.409 -> 0.394 ms; the same for the
+  // flat colours gathered at blend time made the particle frame's 14% slower)
+  static constexpr bool kNullSlot = VTX && K == 1 && !BWD;
+
   __device__ __forceinline__ void init() {
 #pragma unroll
     for (int i = 0; i < K; ++i) s[i] = kSent;
+    if (kNullSlot) c[0] = make_float4(0.f, 0.f, 0.f, 0.f);
     last = kSent;
     r = g = b = 0.f;
     T = 1.f;
@@ -374,7 +381,7 @@ struct PixelState {
           last = x;
         }
       } else {
-        if (s[0] != kSent && live()) {
+        if ((kNullSlot || s[0] != kSent) && live()) {
           blend(s[0], c[0], V);
           last = s[0];
         }
