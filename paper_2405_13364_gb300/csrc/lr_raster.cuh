@@ -643,7 +643,10 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
         const int4 eb = T.eb;
         const uint32_t fl = (uint32_t)eb.z, id = (uint32_t)eb.w;
         if (hashing) hsh += splitmix64(id);
-        if (!st.flagged) {
+        // (the forward discards a flagged pixel's composite, the exact path redoing it, so it
+        // keeps inserting rather than testing the flag per fragment; the backward must not
+        // add a flagged pixel's gradient)
+        if (!BWD || !st.flagged) {
           const float4 kq = T.kq;
           float l1 = 0.f, l2 = 0.f;
           // (the colour-carrying variant keeps one path: its branch cost more than it saved)
