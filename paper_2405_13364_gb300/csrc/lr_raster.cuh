@@ -565,7 +565,12 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
 #pragma unroll
             for (int t = 0; t < 2; ++t)
               if (vsel & (1u << (8 + t))) {
-                qcs[(2 * lane + t) * kSlots] = fc;
+                // zero increments: the fragments' interpolation with the scale 1 (below)
+                // returns fc bit for bit
+                float4* qc = qcs + (2 * lane + t) * kSlots;
+                qc[0] = fc;
+                qc[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                qc[2] = make_float4(0.f, 0.f, 0.f, 0.f);
                 tris[2 * lane + t].eb.z |= (int)kTriFlatCol;
               }
           } else if (LIT && V.color_mode == LR_COLOR_LIT) {
@@ -655,12 +660,12 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
           float4 col = make_float4(0.f, 0.f, 0.f, 0.f);
           if (VTX) {
             const float4* qc = qcs + (2 * c + t) * kSlots;
-            if (fl & kTriFlatCol) {
-              col = qc[0];
-            } else {
+            {
               // perspective-correct colour: interpolated (c / w) divided by the
-              // interpolated 1/w, which is the depth key
-              const float rk = rcp_approx(key);
+              // interpolated 1/w, which is the depth key; a flat-colour triangle of the
+              // batch has zero increments and the scale 1, so a select replaces a branch
+              // per fragment (a0 + l1 * 0 + l2 * 0 and the product by 1 are exact)
+              const float rk = (fl & kTriFlatCol) ? 1.0f : rcp_approx(key);
               const float4 a0 = qc[0], d1 = qc[1], d2 = qc[2];
               col.x = (a0.x + l1 * d1.x + l2 * d2.x) * rk;
               col.y = (a0.y + l1 * d1.y + l2 * d2.y) * rk;
