@@ -370,7 +370,13 @@ struct PixelState {
   }
 
   __device__ __forceinline__ void insert(unsigned long long x, float4 xc, const ViewDev& V) {
-    if (x > last) {   // nearer than a fragment already blended: order not guaranteed
+    // nearer than a fragment already blended: order not guaranteed. The forward pass with
+    // carried colours only records it (the pixel's composite is discarded, so inserting the
+    // fragment anyway is harmless; measured faster than the branch there, slower for the
+    // colours gathered at blend time)
+    if (VTX && !BWD) {
+      flagged |= x > last;
+    } else if (x > last) {
       flagged = true;
       return;
     }
@@ -642,8 +648,11 @@ __global__ __launch_bounds__(kRasterThreads, LR_RASTER_MIN_BLOCKS) void k_raster
       auto frag_step = [&]() {
         const int c = __ffs(m0 | m1) - 1;
         const uint32_t cb = 1u << c;
-        const int t = (m0 & cb) ? 0 : 1;
-        if (t == 0) m0 &= ~cb; else m1 &= ~cb;
+        // the bit leaves m0 if set there, else m1 (no branch on which)
+        const uint32_t in0 = m0 & cb;
+        m0 ^= in0;
+        m1 ^= cb ^ in0;
+        const int t = in0 ? 0 : 1;
         const TriSm& T = tris[2 * c + t];
         const int4 eb = T.eb;
         const uint32_t fl = (uint32_t)eb.z, id = (uint32_t)eb.w;
