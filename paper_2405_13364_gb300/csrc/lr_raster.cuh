@@ -366,7 +366,11 @@ struct PixelState {
       }
       __syncwarp(act);
     }
-    T *= 1.0f - col.w;
+    // T (1 - a) as one fused T - T a (a rounding, not the product's two, away from it: well
+    // inside the colour tolerance); the threshold variant, whose T decides which fragments
+    // blend, and the backward keep the product
+    if (ATH || BWD) T *= 1.0f - col.w;
+    else T = __fmaf_rn(-T, col.w, T);
   }
 
   __device__ __forceinline__ void insert(unsigned long long x, float4 xc, const ViewDev& V) {
