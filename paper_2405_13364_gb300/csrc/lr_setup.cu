@@ -182,13 +182,15 @@ __global__ __launch_bounds__(256) void k_setup(Ws ws) {
     ws.rec_info[g] = info | (worst << 8);
     if (bad) set_error(ws.ctrl, LR_ERR_INVALID_ARG);
   }
-  // statistics: culled quads per reason, one atomic per reason present in the warp (the
-  // host derives the visible count, so warps without a culled quad issue no atomic)
-  if (__ballot_sync(0xffffffffu, active && reason != kVisible)) {
-    for (uint32_t r = kVisible + 1; r <= kNoPixel; ++r) {
-      const unsigned m = __ballot_sync(0xffffffffu, active && reason == r);
-      if (m && (threadIdx.x & 31) == 0) atomicAdd(&ws.ctrl->culled[r], (unsigned long long)__popc(m));
-    }
+  // statistics: culled quads per reason, one atomic per reason present in the warp, by its
+  // lowest lane (the host derives the visible count, so warps without a culled quad issue
+  // no atomic)
+  const unsigned culled = __ballot_sync(0xffffffffu, active && reason != kVisible);
+  if (culled) {
+    const unsigned peers = __match_any_sync(0xffffffffu, active ? reason : kVisible);
+    const int lane = threadIdx.x & 31;
+    if (((culled >> lane) & 1u) && lane == __ffs(peers) - 1)
+      atomicAdd(&ws.ctrl->culled[reason], (unsigned long long)__popc(peers));
   }
 }
 

@@ -226,3 +226,24 @@ def test_deterministic(lr):
     b = gpu_render(lr, s)
     np.testing.assert_array_equal(a["rgba"], b["rgba"])
     np.testing.assert_array_equal(a["hash"], b["hash"])
+
+
+@pytest.mark.parametrize("name", ["frustum256", "layers_flat", "particles"])
+@pytest.mark.parametrize("k", [1, 3])
+def test_carried_flat_colours_bitwise(lr, name, k):
+    # a flat-colour scene through the colour-carrying rasteriser (each triangle's colour with
+    # zero increments and the scale 1) and through the one that gathers colours at blend
+    # time: the same fragments composited in the same order with the same arithmetic, so
+    # the two images are equal bit for bit
+    s = small_scenes()[name]
+    assert s.color_mode == COLOR_FLAT
+    imgs = []
+    for carry in (False, True):
+        r = lr.Renderer(sorter_k=k, carry_colors=carry)
+        out = r.render(lr.DeviceScene.from_scene(s), s.width, s.height, rgba8=True)
+        torch.cuda.synchronize()
+        assert r.stats()["status"] == 0
+        imgs.append((out["rgba"].cpu().numpy().view(np.uint32), out["rgba8"].cpu().numpy()))
+        r.close()
+    np.testing.assert_array_equal(imgs[0][0], imgs[1][0])
+    np.testing.assert_array_equal(imgs[0][1], imgs[1][1])
