@@ -45,15 +45,15 @@ LAUNCHES_PER_FRAME = 9
 RASTER_TRAFFIC = {
     # (DRAM read + write bytes per launch, ncu smsp__issue_active, ncu smsp__inst_executed,
     #  source hash of the captured build)
-    ("layers", 1, False): (102_141_952, 0.7563, 351_803_556, "aea0e283a062082a"),      # profiles/k_raster_layers1080p.md
-    ("particles", 1, False): (383_070_976, 0.6800, 858_778_530, "aea0e283a062082a"),  # profiles/k_raster_particles1080p.md
+    ("layers", 1, False): (102_301_440, 0.7572, 351_803_556, "d4f63243445f2ab1"),      # profiles/k_raster_layers1080p.md
+    ("particles", 1, False): (383_498_496, 0.6758, 847_920_159, "d4f63243445f2ab1"),  # profiles/k_raster_particles1080p.md
 }
 # the same for the rasteriser's variants and the multisample resolve on the layer frame
 # (K = 1): (DRAM bytes per launch, issue-slot share, warp instructions, kernel us, hash)
 VARIANT_CAPTURES = {
-    "alpha_threshold": (93_800_704, 0.7423, 273_373_076, 302.0, "aea0e283a062082a"),   # profiles/k_raster_alpha_layers1080p.md
-    "lit": (117_135_872, 0.5701, 431_126_299, 608.4, "aea0e283a062082a"),               # profiles/k_raster_lit_layers1080p.md
-    "msaa_resolve": (149_113_097, 0.2599, 7_452_000, 26.4, "aea0e283a062082a"),         # profiles/k_resolve_msaa4_layers1080p.md
+    "alpha_threshold": (93_984_256, 0.7434, 273_373_076, 301.1, "d4f63243445f2ab1"),   # profiles/k_raster_alpha_layers1080p.md
+    "lit": (116_781_056, 0.5700, 431_126_299, 609.0, "d4f63243445f2ab1"),               # profiles/k_raster_lit_layers1080p.md
+    "msaa_resolve": (148_978_174, 0.2595, 7_452_000, 26.6, "d4f63243445f2ab1"),         # profiles/k_resolve_msaa4_layers1080p.md
 }
 RASTER_SOURCES = ("lr_raster.cuh", "lr_common.cuh")
 LANES_PER_SM_CLK = 128

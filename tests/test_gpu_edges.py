@@ -118,3 +118,25 @@ def test_mixed_colour_modes_in_one_batch(lr):
                  stats=dict(fragments=int(o["count"].cpu().numpy().astype(np.int64).sum())))
         assert_parity(g, oracle.render(s))
     r.close()
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_concave_and_crossed_quads(lr, seed):
+    # four random vertices per quad within a few pixels: convex, concave and self-crossing
+    # (bow-tie) quads, so the two triangles come with every combination of orientations (the
+    # rasteriser derives one triangle's diagonal coverage from the other's), vertices on
+    # pixel centres half of the time
+    rng = np.random.default_rng(seed)
+    xy = []
+    for i in range(600):
+        c = rng.uniform(4, 92, 2)
+        v = c + rng.uniform(-7, 7, (4, 2))
+        if i % 2:
+            v = np.floor(v) + 0.5
+        xy += [tuple(p) for p in v]
+    cols = np.concatenate([rng.random((600, 3)), rng.uniform(0.1, 0.6, (600, 1))], 1)
+    s = screen_quads_scene(np.array(xy), 96, 96, cols)
+    o = oracle.render(s)
+    for k in (1, 3):
+        g = gpu_render(lr, s, k)
+        assert_parity(g, o)
