@@ -51,8 +51,6 @@ constexpr int kRasterThreads = 256;
 #define LR_RASTER_MIN_BLOCKS 3
 #endif
 constexpr int kRasterWarps = kRasterThreads / 32;
-constexpr int kOvfKeep = 480;               // fragments composited per overflow pass
-constexpr int kOvfBuf = 1024;               // per-warp overflow buffer (power of two)
 constexpr int kOvfThreads = 128;
 // alpha threshold (LR_FLAG_ALPHA_THRESHOLD, the paper's opt-in early stop, Sec. 2 "Sample
 // blending"): a pixel blends a fragment only while its transmittance is above this, i.e.
