@@ -45,15 +45,15 @@ LAUNCHES_PER_FRAME = 9
 RASTER_TRAFFIC = {
     # (DRAM read + write bytes per launch, ncu smsp__issue_active, ncu smsp__inst_executed,
     #  source hash of the captured build)
-    ("layers", 1, False): (102_558_976, 0.7555, 351_803_556, "d125a25d2248362c"),      # profiles/k_raster_layers1080p.md
-    ("particles", 1, False): (383_623_936, 0.6739, 847_920_159, "d125a25d2248362c"),  # profiles/k_raster_particles1080p.md
+    ("layers", 1, False): (101_893_120, 0.7544, 348_696_989, "3e9f8ff852bad3aa"),      # profiles/k_raster_layers1080p.md
+    ("particles", 1, False): (383_102_464, 0.6758, 847_920_159, "3e9f8ff852bad3aa"),  # profiles/k_raster_particles1080p.md
 }
 # the same for the rasteriser's variants and the multisample resolve on the layer frame
 # (K = 1): (DRAM bytes per launch, issue-slot share, warp instructions, kernel us, hash)
 VARIANT_CAPTURES = {
-    "alpha_threshold": (93_521_920, 0.7412, 273_373_076, 300.7, "d125a25d2248362c"),   # profiles/k_raster_alpha_layers1080p.md
-    "lit": (116_823_040, 0.5678, 431_126_299, 610.7, "d125a25d2248362c"),               # profiles/k_raster_lit_layers1080p.md
-    "msaa_resolve": (149_162_753, 0.2631, 7_452_000, 27.0, "d125a25d2248362c"),         # profiles/k_resolve_msaa4_layers1080p.md
+    "alpha_threshold": (93_937_920, 0.7421, 273_373_076, 300.6, "3e9f8ff852bad3aa"),   # profiles/k_raster_alpha_layers1080p.md
+    "lit": (116_687_360, 0.5619, 422_811_933, 605.7, "3e9f8ff852bad3aa"),               # profiles/k_raster_lit_layers1080p.md
+    "msaa_resolve": (149_222_923, 0.2601, 7_452_000, 26.6, "3e9f8ff852bad3aa"),         # profiles/k_resolve_msaa4_layers1080p.md
 }
 RASTER_SOURCES = ("lr_raster.cuh", "lr_common.cuh")
 LANES_PER_SM_CLK = 128
